@@ -1,0 +1,418 @@
+"""Pins for the FP64 oracle against results that the physics or the mathematics fixes.
+
+Each test targets a step of the photon loop (launch, hop, segment, absorption,
+time gate, face/Fresnel, scattering, roulette, detection) and is chosen so that a
+plausible slip in that step (dropped term, wrong sign or index, swapped operands)
+fails it.  None of these tests compares the oracle with itself or with the CUDA path.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C0 = 299.792458
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------------------------- RNG
+def test_splitmix64_published_outputs(orc):
+    for k, hexval in _read_golden("splitmix64_seed0.txt"):
+        assert orc.splitmix64_output(0, int(k)) == int(hexval, 16)
+
+
+def test_uniforms_range_grid_and_moments(orc):
+    u = np.concatenate([orc.uniforms(12345, p, 4096) for p in range(64)])
+    assert u.min() > 0.0 and u.max() < 1.0
+    k = u * 2 ** 24
+    assert np.all(k == np.round(k)) and np.all(np.round(k) % 2 == 1)   # (2k+1) 2^-24
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)         # exact in float
+    n = u.size
+    assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / n)
+    hist, _ = np.histogram(u, bins=64, range=(0, 1))
+    chi2 = ((hist - n / 64) ** 2 / (n / 64)).sum()
+    assert chi2 < 63 + 6 * math.sqrt(2 * 63)
+    r = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(r) < 5 / math.sqrt(n)
+
+
+def test_uniform_streams_independent_per_photon(orc):
+    a = orc.uniforms(7, 0, 2000)
+    b = orc.uniforms(7, 1, 2000)
+    c = orc.uniforms(8, 0, 2000)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.1
+    # a stream is a pure function of (seed, photon id)
+    assert np.array_equal(a, orc.uniforms(7, 0, 2000))
+
+
+# ----------------------------------------------------------------------------- HG
+def _hg_cdf(g, c):
+    """P(cos theta <= c) for the Henyey-Greenstein density, integrated in closed form."""
+    if g == 0:
+        return (c + 1) / 2
+    return (1 - g * g) / (2 * g) * (1 / math.sqrt(1 + g * g - 2 * g * c) - 1 / (1 + g))
+
+
+@pytest.mark.parametrize("g", [-0.5, 0.0, 0.01, 0.5, 0.8, 0.9, 0.95])
+def test_hg_inverse_cdf_matches_closed_form_cdf(orc, g):
+    for xi in np.linspace(0.0005, 0.9995, 401):
+        c = orc.hg_cos(g, xi)
+        assert -1.0 <= c <= 1.0
+        assert abs(_hg_cdf(g, c) - xi) < 1e-9
+
+
+@pytest.mark.parametrize("g", [0.0, 0.5, 0.9])
+def test_hg_mean_cosine_is_g(orc, g):
+    m = 8000
+    xi = (np.arange(m) + 0.5) / m                        # midpoint quadrature over xi
+    c = np.array([orc.hg_cos(g, x) for x in xi])
+    assert abs(np.mean(c) - g) < 2e-4
+
+
+def test_hg_histogram_matches_density(orc):
+    g = 0.8
+    rng = np.random.default_rng(1)
+    xi = rng.random(100_000)
+    c = np.array([orc.hg_cos(g, x) for x in xi])
+    edges = np.linspace(-1, 1, 41)
+    hist, _ = np.histogram(c, bins=edges)
+    expect = np.array([_hg_cdf(g, b) - _hg_cdf(g, a) for a, b in zip(edges[:-1], edges[1:])])
+    expect *= xi.size
+    chi2 = ((hist - expect) ** 2 / expect).sum()
+    assert chi2 < 39 + 6 * math.sqrt(2 * 39)
+
+
+# ----------------------------------------------------------------------------- rotation
+def test_rotation_unit_norm_and_deflection(orc):
+    rng = np.random.default_rng(2)
+    for _ in range(2000):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        ct = rng.uniform(-1, 1)
+        ph = rng.uniform(0, 2 * math.pi)
+        v = orc.rotate(u, ct, ph)
+        assert abs(np.linalg.norm(v) - 1) < 1e-12
+        assert abs(v @ u - ct) < 1e-12
+
+
+def test_rotation_azimuth_is_a_rotation_about_u(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        if abs(u[2]) > 0.99:
+            continue
+        ct = rng.uniform(-0.9, 0.9)
+        st = math.sqrt(1 - ct * ct)
+        p1, p2 = rng.uniform(0, 2 * math.pi, size=2)
+        a = (orc.rotate(u, ct, p1) - ct * u) / st
+        b = (orc.rotate(u, ct, p2) - ct * u) / st
+        assert abs(a @ u) < 1e-12 and abs(np.linalg.norm(a) - 1) < 1e-12
+        # the angle between the two perpendicular components is p2 - p1, with the
+        # sense given by u (right-handed about the propagation direction)
+        assert abs(a @ b - math.cos(p2 - p1)) < 1e-11
+        assert abs(np.cross(a, b) @ u - math.sin(p2 - p1)) < 1e-11
+
+
+def test_rotation_vertical_special_case(orc):
+    for sgn in (1.0, -1.0):
+        v = orc.rotate([0.0, 0.0, sgn], 0.6, 0.3)
+        assert np.allclose(v, [0.8 * math.cos(0.3), 0.8 * math.sin(0.3), sgn * 0.6], atol=1e-14)
+
+
+# ----------------------------------------------------------------------------- Fresnel
+def test_fresnel_normal_incidence_golden(orc):
+    for n1, n2, r0 in _read_golden("fresnel_normal_incidence.txt"):
+        assert abs(orc.fresnel_R(float(n1), float(n2), 1.0) - float(r0)) < 1e-12
+
+
+@pytest.mark.parametrize("n1,n2", [(1.37, 1.0), (1.0, 1.37), (1.45, 1.37), (1.0, 1.5)])
+def test_fresnel_matches_sine_tangent_form(orc, n1, n2):
+    for ti in np.linspace(0.01, 1.55, 80):
+        st = n1 / n2 * math.sin(ti)
+        R = orc.fresnel_R(n1, n2, math.cos(ti))
+        if st >= 1:
+            assert R == 1.0
+            continue
+        tt = math.asin(st)
+        rs = math.sin(ti - tt) ** 2 / math.sin(ti + tt) ** 2
+        rp = math.tan(ti - tt) ** 2 / math.tan(ti + tt) ** 2
+        assert abs(R - 0.5 * (rs + rp)) < 1e-10
+        # transmittance from the amplitude-transmission form closes R + T = 1
+        ci, ct = math.cos(ti), math.cos(tt)
+        ts = 2 * n1 * ci / (n1 * ci + n2 * ct)
+        tp = 2 * n1 * ci / (n2 * ci + n1 * ct)
+        T = 0.5 * (ts * ts + tp * tp) * (n2 * ct) / (n1 * ci)
+        assert abs(R + T - 1) < 1e-10
+        # reciprocity: the same reflectance seen from the other side
+        assert abs(orc.fresnel_R(n2, n1, ct) - R) < 1e-10
+
+
+def test_fresnel_critical_angle(orc):
+    n1, n2 = 1.37, 1.0
+    tc = math.asin(n2 / n1)
+    assert orc.fresnel_R(n1, n2, math.cos(tc + 1e-6)) == 1.0
+    assert orc.fresnel_R(n1, n2, math.cos(tc - 1e-3)) < 1.0
+
+
+# ----------------------------------------------------------------------------- whole walk
+def _slab(nx, ny, nz, media, src=(None,), **kw):
+    labels = np.ones((nz, ny, nx), dtype=np.uint8)
+    base = dict(name="t", labels=labels, voxel_mm=1.0, media=np.array(media, dtype=np.float64),
+                src_kind=0, src_pos=(nx / 2, ny / 2, 0.0), src_dir=(0.0, 0.0, 1.0),
+                waist_mm=0.0, detectors=np.zeros((0, 4)), n_photons=100, n_gates=1,
+                dt_ns=100.0, reflect=1, seed=5)
+    base.update(kw)
+    return workloads.Workload(**base)
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_beer_lambert_column_exact(orc, h):
+    """Purely absorbing medium, index matched to the exterior: every photon runs the
+    beam's voxel column; voxel k absorbs exp(-mua k h) - exp(-mua (k+1) h)."""
+    mua, n = 0.05, 1.37
+    nz = 40
+    dt = 0.01
+    wl = _slab(16, 16, nz, [(0, 0, 1, n), (mua, 0.0, 0.0, n)], voxel_mm=h,
+               src_pos=(8 * h, 8 * h, 0.0), n_photons=50, n_gates=30, dt_ns=dt)
+    r = orc.run(wl, exit_cap=50)
+    E = r.energy / wl.n_photons
+    k = np.arange(nz)
+    expect = np.exp(-mua * k * h) - np.exp(-mua * (k + 1) * h)
+    gate = np.minimum(np.floor(k * h * n / C0 / dt).astype(int), 29)
+    got = E[gate, k, 8, 8]
+    assert np.allclose(got, expect, rtol=1e-10, atol=1e-15)
+    assert abs(E.sum() - (1 - math.exp(-mua * nz * h))) < 1e-12
+    assert np.all(r.exits["fate"] == orc.FATE_ESCAPED)
+    assert np.allclose(r.exits["pos"][:, 2], nz * h)
+    assert np.allclose(r.exits["w"], math.exp(-mua * nz * h))
+    assert np.allclose(r.exits["t"], nz * h * n / C0, rtol=1e-12)
+
+
+def test_time_limit_stops_photon_at_ct(orc):
+    n = 1.37
+    wl = _slab(8, 8, 200, [(0, 0, 1, n), (0.0, 0.0, 0.0, n)], n_photons=10, n_gates=4,
+               dt_ns=0.1)
+    r = orc.run(wl, exit_cap=10)
+    assert np.all(r.exits["fate"] == orc.FATE_TIME)
+    assert np.allclose(r.exits["pos"][:, 2], 0.4 * C0 / n, rtol=1e-12)
+    assert abs(r.tally["time_exceeded"] - 10) < 1e-12
+
+
+def test_fresnel_slab_escape_series(orc):
+    """Non-scattering, non-absorbing slab (n 1.37 in air) at normal incidence: the photon
+    bounces between the faces and leaves through the far face with p = 1/(1 + R0)."""
+    n1 = 1.37
+    N = 40000
+    wl = _slab(8, 8, 16, [(0, 0, 1, 1.0), (0.0, 0.0, 0.0, n1)], src_pos=(4.0, 4.0, 0.0),
+               n_photons=N, dt_ns=1000.0)
+    r = orc.run(wl, exit_cap=N)
+    R0 = ((n1 - 1) / (n1 + 1)) ** 2
+    far = np.mean(r.exits["pos"][:, 2] == 16.0)
+    p = 1 / (1 + R0)
+    assert abs(far - p) < 5 * math.sqrt(p * (1 - p) / N)
+    assert np.all(r.exits["fate"] == orc.FATE_ESCAPED)
+    # exits leave along the normal, at the face, undeflected
+    assert np.allclose(np.abs(r.exits["dir"][:, 2]), 1.0)
+
+
+def test_fresnel_slab_with_absorption(orc):
+    """Same slab with absorption A = exp(-mua D) per crossing: the expected weight leaving
+    the far face is (1-R0) A / (1 - R0^2 A^2)."""
+    n1, mua, D = 1.37, 0.02, 16.0
+    N = 40000
+    wl = _slab(8, 8, 16, [(0, 0, 1, 1.0), (mua, 0.0, 0.0, n1)], src_pos=(4.0, 4.0, 0.0),
+               n_photons=N, dt_ns=1000.0)
+    r = orc.run(wl, exit_cap=N)
+    R0 = ((n1 - 1) / (n1 + 1)) ** 2
+    A = math.exp(-mua * D)
+    ex = r.exits
+    far_w = ex["w"][ex["pos"][:, 2] == D].sum() / N
+    expect = (1 - R0) * A / (1 - R0 * R0 * A * A)
+    # each far exit carries A^(2k+1); the spread is bounded by the binomial spread
+    assert abs(far_w - expect) < 5 * math.sqrt(expect * (1 - expect) / N)
+    # every exit weight is an odd (far) or even (near) power of A
+    k = np.log(ex["w"]) / math.log(A)
+    assert np.allclose(k, np.round(k), atol=1e-9)
+    assert np.all((np.round(k) % 2 == 1) == (ex["pos"][:, 2] == D))
+
+
+def test_snell_refraction_on_ballistic_ray(orc):
+    """Oblique non-scattering ray through an n=1.0 | n=1.5 interface at z = 8 mm, with the
+    exterior matched to the lower layer: every bottom exit lies where Snell's law puts it
+    (with 0, 1, 2... round trips in the upper layer) and leaves at the refracted angle."""
+    nx = 200
+    labels = np.ones((32, 4, nx), dtype=np.uint8)
+    labels[8:] = 2
+    th = math.radians(25.0)
+    wl = workloads.Workload("snell", labels, 1.0,
+                            np.array([(0, 0, 1, 1.5), (0, 0, 0, 1.0), (0, 0, 0, 1.5)]), 0,
+                            (10.3, 2.0, 0.0), (math.sin(th), 0.0, math.cos(th)), 0.0,
+                            np.zeros((0, 4)), 4000, 1, 1000.0, 1, 9)
+    r = orc.run(wl, exit_cap=4000)
+    ex = r.exits
+    bottom = ex[np.isclose(ex["pos"][:, 2], 32.0)]
+    tt = math.asin(math.sin(th) / 1.5)
+    assert len(bottom) > 3000
+    # the horizontal distance travelled: 8 tan(th) + 16 tan(th) per round trip + 24 tan(tt)
+    x = bottom["pos"][:, 0] - 10.3 - 8 * math.tan(th) - 24 * math.tan(tt)
+    trips = x / (16 * math.tan(th))
+    assert np.allclose(trips, np.round(trips), atol=1e-9)
+    assert np.allclose(bottom["dir"][:, 0], math.sin(tt), atol=1e-12)
+    assert np.allclose(bottom["dir"][:, 2], math.cos(tt), atol=1e-12)
+    # photons transmitted at the first interface: fraction 1 - R(25 deg, 1.0 -> 1.5)
+    R = orc.fresnel_R(1.0, 1.5, math.cos(th))
+    first = np.sum(np.round(trips) == 0) / 4000
+    assert abs(first - (1 - R)) < 5 * math.sqrt(R * (1 - R) / 4000)
+
+
+def test_gaussian_source_moments(orc):
+    """Ballistic, index-matched: exit points reproduce the launch profile
+    I(r) ~ exp(-2 r^2 / w^2), i.e. P(r > rho) = exp(-2 rho^2 / w^2)."""
+    w = 2.0
+    N = 20000
+    wl = _slab(64, 64, 8, [(0, 0, 1, 1.37), (0, 0, 0, 1.37)], src_kind=1,
+               src_pos=(32.0, 32.0, 0.0), waist_mm=w, n_photons=N)
+    r = orc.run(wl, exit_cap=N)
+    p = r.exits["pos"]
+    assert np.allclose(p[:, 2], 8.0)
+    dx, dy = p[:, 0] - 32.0, p[:, 1] - 32.0
+    assert abs(dx.mean()) < 5 * (w / 2) / math.sqrt(N)
+    assert abs(dy.mean()) < 5 * (w / 2) / math.sqrt(N)
+    assert abs(np.mean(dx * dx) - w * w / 4) < 0.05 * w * w / 4
+    rr = np.sort(np.hypot(dx, dy))
+    cdf = 1 - np.exp(-2 * rr ** 2 / w ** 2)
+    ks = np.max(np.abs(cdf - np.arange(1, N + 1) / N))
+    assert ks < 1.63 / math.sqrt(N)                    # KS at about the 1% level
+
+
+def test_launch_outside_medium_is_missed(orc):
+    wl = _slab(8, 8, 8, [(0, 0, 1, 1.0), (0.01, 10, 0.9, 1.37)], src_pos=(-3.0, 4.0, 0.0),
+               n_photons=5)
+    r = orc.run(wl, exit_cap=5)
+    assert np.all(r.exits["fate"] == orc.FATE_MISSED)
+    assert r.tally["escaped"] == 5 and r.tally["absorbed"] == 0
+
+
+def _balance(t):
+    return t["absorbed"] + t["escaped"] + t["time_exceeded"] + t["roulette_killed"] \
+        - t["roulette_gained"]
+
+
+@pytest.mark.parametrize("name,reflect", [("c2", 1), ("c2", 0), ("b2", 1), ("c3", 1)])
+def test_energy_balance_exact(orc, name, reflect):
+    wl = workloads.by_name(name, n_photons=300)
+    if name == "c3":
+        wl = wl.with_(labels=wl.labels[:40, 96:160, 96:160].copy(), src_pos=(16.0, 16.0, 0.0))
+    r = orc.run(wl, reflect=reflect, rr_threshold=2e-2)
+    t = r.tally
+    assert t["launched"] == 300
+    assert abs(_balance(t) - 300) < 1e-9 * 300
+    assert abs(r.energy.sum() - t["absorbed"]) < 1e-9 * 300
+    assert t["roulette_killed"] > 0
+
+
+def test_detector_weight_identity(orc):
+    """Fresnel and scattering leave the weight alone, so a detected photon carries
+    exp(-sum_m mua_m L_m) times m^k for its k roulette survivals."""
+    wl = workloads.c2(n_photons=4000)
+    mua = wl.media[:, 0]
+    for thr in (0.0, 1e-2):
+        r = orc.run(wl, rr_threshold=thr)
+        rec = r.det_rec
+        assert rec.shape[0] > 10
+        L = rec[:, 11:]
+        expect = np.exp(-(L * mua[1:]).sum(axis=1)) * 10.0 ** rec[:, 10]
+        assert np.allclose(rec[:, 3], expect, rtol=1e-10)
+        # the exit point lies in the detector's disk on the z = 0 face
+        d = rec[:, 1].astype(int)
+        c = wl.detectors[d]
+        assert np.all((rec[:, 4] - c[:, 0]) ** 2 + (rec[:, 5] - c[:, 1]) ** 2 <= c[:, 3] ** 2)
+        assert np.all(rec[:, 6] == 0.0) and np.all(rec[:, 9] < 0)
+        # photon-id order, at most one record per photon
+        assert np.all(np.diff(rec[:, 0]) > 0)
+        # partial paths add up to the total path c t / n only in one medium; here check
+        # that they are non-negative and the scattered count is positive
+        assert np.all(L >= 0) and np.all(rec[:, 2] >= 1)
+
+
+def test_roulette_survival_fraction(orc):
+    """Survivors carry m w: the killed weight is (m - 1) times the pre-roulette weight of
+    the survivors on average, i.e. killed ~= gained."""
+    wl = _slab(32, 32, 32, [(0, 0, 1, 1.37), (0.5, 5.0, 0.5, 1.37)], src_pos=(16.0, 16.0, 0.0),
+               n_photons=20000)
+    r = orc.run(wl, rr_threshold=0.05, rr_m=10.0)
+    t = r.tally
+    nrr = r.count["roulette"]
+    assert nrr > 5000
+    assert abs(t["roulette_gained"] / t["roulette_killed"] - 1.0) < 0.1
+
+
+def test_results_independent_of_thread_count(orc):
+    wl = workloads.c2(n_photons=400)
+    a = orc.run(wl, n_threads=1, exit_cap=400)
+    b = orc.run(wl, n_threads=3, exit_cap=400)
+    assert np.array_equal(a.exits, b.exits)
+    assert np.allclose(a.energy, b.energy, rtol=1e-12, atol=1e-15)
+    assert np.array_equal(a.det_rec, b.det_rec)
+
+
+def test_photon_ranges_compose(orc):
+    """A run over [0, N) equals the union of runs over [0, k) and [k, N) (the basis for
+    sharding photons across ranks)."""
+    wl = workloads.c2(n_photons=300)
+    full = orc.run(wl, exit_cap=300)
+    a = orc.run(wl, n_photons=120, exit_cap=120)
+    b = orc.run(wl, n_photons=180, photon_offset=120, exit_cap=180)
+    assert np.array_equal(np.concatenate([a.exits, b.exits]), full.exits)
+    assert np.allclose(a.energy + b.energy, full.energy, rtol=1e-12, atol=1e-15)
+    for k in full.tally:
+        assert abs(a.tally[k] + b.tally[k] - full.tally[k]) < 1e-9
+
+
+@pytest.mark.slow
+def test_diffusion_far_field(orc):
+    """Homogeneous semi-infinite-like medium (64^3, mua 0.01, mus' 1.0, n 1.37 in air):
+    away from the source the time-integrated fluence follows the extrapolated-boundary
+    diffusion solution (point source at z0 = 1/mus', image at -(z0 + 2 zb), zb = 2 A D,
+    A from the effective internal reflection of the n = 1.37 / air boundary)."""
+    wl = workloads.c1(n_photons=100_000, seed=4)
+    r = orc.run(wl)
+    mua, mus, g, n = wl.media[1]
+    E = r.energy.sum(axis=0)
+    phi = E / (mua * wl.n_photons)                  # 1/mm^2, time-integrated
+    mus_p = mus * (1 - g)
+    D = 1.0 / (3 * (mua + mus_p))
+    mueff = math.sqrt(mua / D)
+    nrel = n
+    reff = -1.440 / nrel ** 2 + 0.710 / nrel + 0.668 + 0.0636 * nrel
+    A = (1 + reff) / (1 - reff)
+    z0 = 1.0 / (mua + mus_p)
+    zb = 2 * A * D
+    zc = np.arange(64) + 0.5
+    X, Y = np.meshgrid(zc - 32.0, zc - 32.0, indexing="xy")
+    rho2 = X ** 2 + Y ** 2
+    mask = rho2 <= 5.0 ** 2
+    ratios = []
+    for k in range(6, 22, 2):
+        z = zc[k]
+        r1 = np.sqrt(rho2 + (z - z0) ** 2)
+        r2 = np.sqrt(rho2 + (z + z0 + 2 * zb) ** 2)
+        dif = (np.exp(-mueff * r1) / r1 - np.exp(-mueff * r2) / r2) / (4 * math.pi * D)
+        ratios.append(phi[k][mask].sum() / dif[mask].sum())
+    ratios = np.array(ratios)
+    assert np.all(np.abs(ratios - 1) < 0.12), ratios
