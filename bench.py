@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the voxel Monte Carlo photon walk on GB300 (photons/ms).
+
+One step = one complete simulation (zero outputs, persistent walk kernel over every photon,
+FP64 tally reduction) of the heterogeneous two-sphere workload: 64^3 voxels of 1 mm, two
+overlapping spherical inclusions, 1e8 photons, 10 time gates of 0.5 ns, four r = 2 mm disk
+detectors recording partial path lengths.  Inputs are resident in HBM when the timed region
+starts; `e2e` repeats the measurement through the C ABI with host buffers (label upload and
+fluence/tally/detected-record read-back inside the timed region).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): each rank simulates its own photon-id range of the
+same size (weak scaling; photon ranges are independent, so there is no data-path
+collective); the max step time over ranks gives the job throughput.  `--impl reference`
+times the FP64 CPU oracle on bounded samples of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "photons/ms on one GB300"
+UNIT = "photons/ms"
+WORKLOAD = "c2_two_spheres_64"
+WORKLOAD_DESC = ("64^3 x 1 mm label volume, background (mua 0.01, mus 10, g 0.9, n 1.37) with "
+                 "spheres r=10 @ (32,32,24) and r=8 @ (20,40,30), pencil beam (32,32,0) +z, "
+                 "1e8 photons, 10 gates x 0.5 ns, 4 disk detectors r=2 mm on z=0")
+
+# Algorithmic thread-operations per event of the walk (counted from the algorithm's
+# arithmetic, independent of the compiled code): every segment (face distances, event
+# selection, gate, advance, absorption, run-length accumulation), a hop draw, a
+# scattering event (2 uniforms, HG, azimuth, rotation, 3 reciprocals, roulette test), a
+# face crossing, a Fresnel evaluation, a fluence flush, and a photon launch + finish.
+OPS = {"segment": 35, "hop": 17, "scatter": 65, "face": 15, "fresnel": 25, "flush": 3,
+       "photon": 60}
+SM_COUNT = 152
+LANES_PER_SM = 128          # 4 SM sub-partitions x 32 lanes issue per clock
+
+
+def algorithmic_ops(stats: dict, tally: dict) -> float:
+    seg = stats["scatter"] + stats["face"] + stats["photons"]
+    hop = stats["scatter"] + stats["photons"]
+    return (OPS["segment"] * seg + OPS["hop"] * hop + OPS["scatter"] * stats["scatter"] +
+            OPS["face"] * stats["face"] + OPS["fresnel"] * stats["fresnel"] +
+            OPS["flush"] * stats["flush"] + OPS["photon"] * stats["photons"])
+
+
+def peaks() -> dict:
+    p = {"sm_max_mhz": 2070.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        p["sm_max_mhz"] = float(d.get("sm_max_mhz", 2070.0))
+        p["source"] = "measured"
+    return p
+
+
+def walk_traffic():
+    """DRAM bytes per walk launch from the committed ncu summary, if it was taken on the
+    current kernel source (matching hash); otherwise None."""
+    src = os.path.join(ROOT, "paper_1711_03244_gb300", "csrc", "walk.cu")
+    prof = os.path.join(ROOT, "profiles", "walk_kernel_c2.md")
+    if not os.path.exists(prof):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(prof).read()
+    m_h = re.search(r"walk\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
+    if m_h and m_b and m_h.group(1) == h:
+        return float(m_b.group(1))
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, wl, world, rank):
+    """FP64 CPU oracle on bounded samples of the same workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = args.ref_photons
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.run(wl, n_photons=max(n // 10, 1), energy=True, n_threads=cores)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(wl, n_photons=n, photon_offset=k * n, energy=True, n_threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / ms
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "photons_per_step": n,
+                       "note": "each step is a bounded sample of the workload's photons"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} photons of {WORKLOAD} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--photons", type=int, default=100_000_000)
+    ap.add_argument("--ref-photons", type=int, default=20_000)
+    ap.add_argument("--cpu-photons", type=int, default=50_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world, rank, local = dist_env()
+    wl = workloads.c2(n_photons=args.photons)
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+        return
+
+    import torch
+    import paper_1711_03244_gb300 as mcx
+    from paper_1711_03244_gb300 import build as mcx_build
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(mcx.LIB_PATH):
+        mcx_build.build()
+    if dist is not None:
+        dist.barrier()
+    mcx.load()
+
+    stream = torch.cuda.current_stream()
+    sim = mcx.Simulation.from_workload(wl)
+    offset, n = mcx.photon_range(rank, world, wl.n_photons)   # this rank's photon ids
+
+    def step():
+        cfg = mcx.mcx_run_cfg_default(n_photons=n, photon_offset=offset, n_gates=wl.n_gates,
+                                      dt_ns=wl.dt_ns, seed=wl.seed,
+                                      max_detected=wl.max_detected, cuda_stream=stream)
+        mcx.mcx_run(sim.handle, cfg)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+        mcx.mcx_sync(sim.handle, allow_cap=True)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    walk_ms = []
+    stats = tally = None
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                   # L2 (129 MB) flushed between timed steps
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            walk_ms.append(mcx.mcx_last_kernel_ms(sim.handle))
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = mcx.mcx_read_stats(sim.handle)
+    tally = mcx.mcx_read_tally(sim.handle)
+    info = mcx.mcx_launch_info(sim.handle)
+    total_ms = float(sum(step_ms))
+    walk_avg = float(np.mean(walk_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms, walk_avg], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, walk_avg = float(t[0]), float(t[1])
+    value = world * n * args.steps / total_ms
+
+    # ---- e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    labels_pinned = torch.from_numpy(wl.labels).pin_memory()
+    flu_pinned = torch.empty((wl.n_gates,) + wl.labels.shape, dtype=torch.float32).pin_memory()
+    e2e_times = []
+    h2d = d2h = 0
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mcx.mcx_update_labels(sim.handle, labels_pinned.numpy())
+        mcx.mcx_set_media(sim.handle, wl.media)
+        step()
+        mcx.mcx_sync(sim.handle, allow_cap=True)
+        mcx.mcx_read_fluence(sim.handle, flu_pinned.numpy(), normalized=True)
+        tl = mcx.mcx_read_tally(sim.handle)
+        rec, tot = mcx.mcx_read_detected(sim.handle)
+        dt = time.perf_counter() - t0
+        if k > 0:                             # the first pass warms the read path
+            e2e_times.append(dt)
+        h2d = wl.labels.nbytes + wl.media.astype(np.float32).nbytes
+        d2h = flu_pinned.numel() * 4 + 6 * 8 + rec.nbytes
+    e2e_ms = 1e3 * float(np.mean(e2e_times))
+    e2e_val = world * n / e2e_ms
+
+    # ---- roofline of the walk kernel: algorithmic thread-ops / launch time vs issue peak
+    pk = peaks()
+    ops = algorithmic_ops(stats, tally)                   # per launch on this rank
+    achieved = ops / (walk_avg * 1e-3) / 1e12             # T thread-op/s
+    peak = SM_COUNT * LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tthread-op/s",
+            "frac": achieved / peak, "traffic": walk_traffic(),
+            "peak_note": f"152 SMs x 128 lanes x {pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)",
+            "ops_per_photon": ops / n, "kernel": "walk_kernel<float,true>",
+            "walk_ms": walk_avg}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "photons_per_step": n,
+                       "photons_per_rank": n, "seed": wl.seed,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "launch": info, "parallelism": f"photon-id ranges x{world}"},
+            "gpu_launches": 4 * args.steps,
+            "wall_s": wall,
+            "clocks": clk.summary(),
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+            "events": {k: int(v) for k, v in stats.items()},
+            "energy_balance_rel": abs(tally["absorbed"] + tally["escaped"] +
+                                      tally["time_exceeded"] + tally["roulette_killed"] -
+                                      tally["roulette_gained"] - tally["launched"]) /
+            max(tally["launched"], 1.0)}
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        nc = args.cpu_photons
+        t0 = time.perf_counter()
+        oracle.run(wl, n_photons=nc, energy=True, n_threads=cores)
+        cpu_ms = 1e3 * (time.perf_counter() - t0)
+        line["cpu_baseline"] = {"value": nc / cpu_ms, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {nc} photons of {WORKLOAD} (FP64 oracle, "
+                                          f"{cores} OpenMP threads, {cpu_ms / 1e3:.1f} s)"}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

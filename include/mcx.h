@@ -1,0 +1,206 @@
+/*
+ * mcx.h - C ABI of the GB300 voxel Monte Carlo photon-transport library.
+ *
+ * The operation is the paper's photon simulation workflow (Fig. 1 and the paragraph that
+ * describes it): the host processes the user's inputs (domain, optical properties, source,
+ * photon count), the device runs the photon simulation loop in every thread with
+ * independent random streams, and the host reads back the 3-D fluence maps and the
+ * detected-photon data, then post-processes them.  The photon loop's physics is the one
+ * the paper's benchmark description (beside Fig. 2) relies on: exponential hops through a
+ * labelled voxel domain, Snell/Fresnel at refractive-index mismatches (or termination at
+ * the boundary), Henyey-Greenstein scattering, Russian roulette, atomic (race-free)
+ * fluence accumulation into time gates, and disk detectors recording partial path lengths.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an mcx_status; no call aborts or throws across the ABI.  On an
+ *     error, mcx_last_error(sim) describes it (mcx_last_error(NULL) for errors raised
+ *     before a handle exists).
+ *   - Inputs passed as host pointers are copied before the call returns; the caller keeps
+ *     ownership.  Outputs are written to caller-owned buffers.
+ *   - Positions and lengths are in mm, times in ns, coefficients in 1/mm.
+ *   - Label volumes are uint8 arrays [nz][ny][nx] (x fastest).  Label 0, and everything
+ *     outside the grid, is the exterior medium.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - Needs a CUDA device of compute capability 10.3 (GB300); the library is built for
+ *     sm_103a only.
+ */
+#ifndef MCX_H
+#define MCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MCX_ABI_VERSION 1
+
+typedef struct mcx_sim mcx_sim;   /* opaque; owns all device buffers of one simulation */
+
+typedef enum mcx_status {
+    MCX_OK = 0,
+    MCX_E_ARG = -1,      /* invalid argument; nothing was changed */
+    MCX_E_STATE = -2,    /* call out of order (e.g. run before media are set) */
+    MCX_E_CUDA = -3,     /* a CUDA call failed; see mcx_last_error */
+    MCX_E_OOM = -4,      /* device allocation failed */
+    MCX_E_CAP = -5,      /* outputs are valid, but a capacity was hit: the detected-photon
+                            buffer overflowed or a photon reached the per-photon event cap */
+    MCX_E_TIMEOUT = -6   /* mcx_sync gave up waiting; the run is still in flight */
+} mcx_status;
+
+/* photon fates (mcx_exit.fate) */
+enum { MCX_FATE_NONE = 0, MCX_FATE_ESCAPED = 1, MCX_FATE_ROULETTE = 2, MCX_FATE_TIME = 3,
+       MCX_FATE_MISSED = 4, MCX_FATE_CAPPED = 5 };
+
+/* energy tallies (mcx_read_tally); launched = absorbed + escaped + time_exceeded
+   + roulette_killed - roulette_gained holds up to rounding */
+enum { MCX_TALLY_LAUNCHED = 0, MCX_TALLY_ABSORBED = 1, MCX_TALLY_ESCAPED = 2,
+       MCX_TALLY_TIME = 3, MCX_TALLY_RR_KILLED = 4, MCX_TALLY_RR_GAINED = 5, MCX_NTALLY = 6 };
+
+/* event counters (mcx_read_stats): scattering events, voxel-face crossings, Fresnel
+   evaluations (including total internal reflection), fluence atomics issued, roulette
+   draws, photons finished (all fates), photons detected, photons stopped by the cap */
+enum { MCX_STAT_SCATTER = 0, MCX_STAT_FACE = 1, MCX_STAT_FRESNEL = 2, MCX_STAT_FLUSH = 3,
+       MCX_STAT_ROULETTE = 4, MCX_STAT_PHOTONS = 5, MCX_STAT_DETECTED = 6, MCX_STAT_CAPPED = 7,
+       MCX_NSTAT = 8 };
+
+/* Per-run settings.  Fill with mcx_run_cfg_default() and then override fields. */
+typedef struct mcx_run_cfg {
+    uint32_t struct_size;          /* sizeof(mcx_run_cfg); checked by mcx_run */
+    uint32_t n_gates;              /* time gates [g dt, (g+1) dt), g < n_gates; >= 1 */
+    uint64_t n_photons;            /* photons launched by this run (may be 0) */
+    uint64_t photon_offset;        /* id of the first photon; a run over ids [a, a+n) is a
+                                      pure function of (seed, a, n), so ranges compose */
+    uint64_t seed;                 /* run seed; photon p's stream derives from (seed, p) */
+    float dt_ns;                   /* gate width, > 0; photons stop at n_gates * dt_ns */
+    int32_t reflect;               /* 1: Fresnel/Snell at index mismatches; 0: photons are
+                                      terminated on reaching the exterior and pass internal
+                                      mismatches unchanged (the paper's benchmark B1) */
+    float rr_threshold;            /* Russian roulette below this weight (0 disables) */
+    float rr_m;                    /* roulette: survive with probability 1/rr_m, weight x rr_m */
+    uint64_t max_detected;         /* capacity of the detected-photon buffer (records) */
+    uint64_t exit_log;             /* log fate/exit of photons offset .. offset+exit_log-1 */
+    uint64_t max_events_per_photon;/* segment cap per photon (0 = library default 1e8) */
+    int32_t accum_mode;            /* 0: FP32 register run-length + global FP32 atomics */
+    int32_t block_size;            /* threads per block, multiple of 32 (0 = 256) */
+    int32_t grid_size;             /* persistent blocks (0 = SMs x resident blocks/SM) */
+    int32_t precision;             /* 0: FP32 photon state (the product path); 1: the same walk
+                                      in FP64, a trajectory-parity diagnostic that runs at the
+                                      part's much lower FP64 rate */
+    void *cuda_stream;             /* cudaStream_t to enqueue on (NULL = legacy default) */
+} mcx_run_cfg;
+
+/* Fate and end state of one logged photon (fixed-seed parity log). */
+typedef struct mcx_exit {
+    int32_t fate;                  /* MCX_FATE_* */
+    uint32_t nscat;                /* scattering events */
+    float pos[3];                  /* mm: exit point for escaped photons, else end point */
+    float dir[3];                  /* direction at the end (refracted on escape) */
+    float w;                       /* weight at the end */
+    float t;                       /* ns */
+} mcx_exit;
+
+/* ABI version of the loaded library (MCX_ABI_VERSION it was built with). */
+int32_t mcx_abi_version(void);
+const char *mcx_status_string(int32_t status);
+void mcx_run_cfg_default(mcx_run_cfg *cfg);
+
+/* Creates a simulation over an nx x ny x nz label volume of cubic voxels voxel_mm wide.
+   labels: uint8 [nz][ny][nx]; a host pointer (labels_on_device = 0) or a device pointer on
+   the current device (labels_on_device = 1); copied into the handle's device memory.
+   The handle binds to the CUDA device current at this call.  nx*ny*nz < 2^32. */
+mcx_status mcx_create_volume(mcx_sim **out, uint32_t nx, uint32_t ny, uint32_t nz,
+                             float voxel_mm, const uint8_t *labels, int32_t labels_on_device);
+
+/* Replaces the label volume (same dimensions); invalidates previous outputs. */
+mcx_status mcx_update_labels(mcx_sim *sim, const uint8_t *labels, int32_t labels_on_device);
+
+/* Optical properties, host array props[n_media][4] = (mua /mm, mus /mm, g, n); row m
+   applies to label m; row 0 is the exterior (only its n is used).  1 <= n_media <= 256;
+   every label present in the volume must have a row.  mua, mus >= 0, |g| < 1, n > 0. */
+mcx_status mcx_set_media(mcx_sim *sim, uint32_t n_media, const float *props);
+
+/* Source: kind 0 = pencil beam at pos along dir; kind 1 = Gaussian beam whose launch
+   points are spread over the plane normal to dir with I(r) ~ exp(-2 r^2 / waist^2).
+   dir is normalised by the library.  A photon whose launch point is outside the grid or
+   in a label-0 voxel is counted as escaped with fate MCX_FATE_MISSED. */
+mcx_status mcx_set_source(mcx_sim *sim, int32_t kind, const float pos_mm[3],
+                          const float dir[3], float waist_mm);
+
+/* Adds a detector: a photon escaping at a point within radius_mm of center_mm is recorded
+   (lowest detector id on overlap).  Up to 64 detectors; with detectors present the number
+   of media is limited to 33 (32 tissue labels, for the partial-path record). */
+mcx_status mcx_add_detector(mcx_sim *sim, const float center_mm[3], float radius_mm,
+                            int32_t *out_id);
+mcx_status mcx_clear_detectors(mcx_sim *sim);
+
+/* Enqueues one simulation on cfg->cuda_stream and returns without waiting.  Zeroes the
+   outputs, runs the persistent photon-walk kernel, then reduces the energy tallies.
+   Output buffers are (re)allocated here when the gate count or capacities change. */
+mcx_status mcx_run(mcx_sim *sim, const mcx_run_cfg *cfg);
+
+/* Waits for the last run, polling for at most timeout_s seconds (< 0: no limit).
+   MCX_E_TIMEOUT leaves the run in flight.  MCX_E_CAP: finished, but a capacity was hit. */
+mcx_status mcx_sync(mcx_sim *sim, double timeout_s);
+
+/* Device time of the last run's walk kernel (CUDA events on the run's stream), in ms.
+   Waits for the run. */
+mcx_status mcx_last_kernel_ms(mcx_sim *sim, float *ms);
+
+/* Fluence of the last run, float [n_gates][nz][ny][nx].  normalized = 0: absorbed weight
+   per voxel and gate (sum of deposited photon weight).  normalized = 1: fluence rate per
+   launched photon, E / (mua h^3 N dt) in 1/(mm^2 ns), 0 where mua = 0.  dst is host memory
+   (dst_on_device = 0; the call waits) or device memory on the handle's device
+   (dst_on_device = 1; the copy is enqueued on the run's stream).  n_elems must equal
+   n_gates*nx*ny*nz. */
+mcx_status mcx_read_fluence(mcx_sim *sim, float *dst, uint64_t n_elems, int32_t normalized,
+                            int32_t dst_on_device);
+
+/* Words (4 bytes each) per detected-photon record: 12 + (n_media - 1). */
+int32_t mcx_detected_stride(const mcx_sim *sim);
+
+/* Detected-photon records of the last run, in photon-id order, into host memory dst
+   (cap_records * stride words).  Record layout, 32-bit words:
+     [0] photon id low 32 bits, [1] high 32 bits (uint32 bit patterns)
+     [2] detector id (int32)   [3] scattering events (uint32)
+     [4] exit weight (float)   [5..7] exit point (mm)   [8..10] exit direction
+     [11] roulette survivals (uint32)   [12 + m - 1] path length in label m (mm), m >= 1
+   n_written: records copied; n_total: photons detected (more than the buffer held when the
+   buffer overflowed).  Waits for the run. */
+mcx_status mcx_read_detected(mcx_sim *sim, void *dst, uint64_t cap_records,
+                             uint64_t *n_written, uint64_t *n_total);
+
+/* Energy tallies (MCX_TALLY_*) of the last run, FP64, into host memory.  Waits. */
+mcx_status mcx_read_tally(mcx_sim *sim, double out[MCX_NTALLY]);
+
+/* Event counters (MCX_STAT_*) of the last run into host memory.  Waits. */
+mcx_status mcx_read_stats(mcx_sim *sim, uint64_t out[MCX_NSTAT]);
+
+/* Exit log of the last run (photons offset .. offset + exit_log - 1, by photon id) into
+   host memory.  Waits. */
+mcx_status mcx_read_exits(mcx_sim *sim, mcx_exit *dst, uint64_t cap, uint64_t *n_written);
+
+/* Launch shape the last run used (blocks, threads per block, resident blocks per SM,
+   registers per thread). */
+mcx_status mcx_launch_info(mcx_sim *sim, int32_t out[4]);
+
+const char *mcx_last_error(const mcx_sim *sim);
+void mcx_destroy(mcx_sim *sim);
+
+/* ---- diagnostics: run the library's device primitives on small host arrays ---------- */
+
+/* First n uniforms of photon `photon`'s stream for `seed`, as the walk kernel draws them. */
+mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *out_host);
+
+/* Evaluates one device primitive on n input tuples (host arrays, row-major):
+     kind 0: Henyey-Greenstein sample,  in (g, xi)                             -> out (cos, sin)
+     kind 1: direction rotation,        in (ux, uy, uz, cos_t, sin_t, phi/2pi) -> out (ux, uy, uz)
+     kind 2: Fresnel reflectance,       in (n1, n2, cos_i)                     -> out (R; 1 on TIR) */
+mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
+                               float *out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCX_H */

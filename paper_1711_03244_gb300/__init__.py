@@ -1,0 +1,393 @@
+"""Python binding of the GB300 voxel Monte Carlo photon-transport library.
+
+Argument marshalling only: every step of the photon walk, the output zeroing, the tally
+reduction, the fluence normalisation and the detected-record ordering run in the CUDA
+library `libmcx_gb300.so` (built in-tree for sm_103a by `build.py`).  There is no CPU
+fallback: importing this package without the built library raises ImportError, and the
+library itself needs a GB300 (compute capability 10.3).
+
+The functions keep the C names of `include/mcx.h` (mcx_create_volume, mcx_set_media, ...).
+Host arrays are NumPy arrays; device buffers may be torch CUDA tensors, whose data_ptr()
+is passed through, and the CUDA stream may be a torch.cuda.Stream (PyTorch is used only
+for device memory and streams).  `Simulation` is a small convenience wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmcx_gb300.so")
+
+MCX_OK, MCX_E_ARG, MCX_E_STATE, MCX_E_CUDA, MCX_E_OOM, MCX_E_CAP, MCX_E_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
+FATE_NONE, FATE_ESCAPED, FATE_ROULETTE, FATE_TIME, FATE_MISSED, FATE_CAPPED = range(6)
+TALLY_NAMES = ("launched", "absorbed", "escaped", "time_exceeded", "roulette_killed",
+               "roulette_gained")
+STAT_NAMES = ("scatter", "face", "fresnel", "flush", "roulette", "photons", "detected",
+              "capped")
+REC_BASE = 12
+
+
+class McxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class McxRunCfg(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("n_gates", ctypes.c_uint32),
+        ("n_photons", ctypes.c_uint64),
+        ("photon_offset", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64),
+        ("dt_ns", ctypes.c_float),
+        ("reflect", ctypes.c_int32),
+        ("rr_threshold", ctypes.c_float),
+        ("rr_m", ctypes.c_float),
+        ("max_detected", ctypes.c_uint64),
+        ("exit_log", ctypes.c_uint64),
+        ("max_events_per_photon", ctypes.c_uint64),
+        ("accum_mode", ctypes.c_int32),
+        ("block_size", ctypes.c_int32),
+        ("grid_size", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class McxExit(ctypes.Structure):
+    _fields_ = [("fate", ctypes.c_int32), ("nscat", ctypes.c_uint32),
+                ("pos", ctypes.c_float * 3), ("dir", ctypes.c_float * 3),
+                ("w", ctypes.c_float), ("t", ctypes.c_float)]
+
+
+EXIT_DTYPE = np.dtype([("fate", np.int32), ("nscat", np.uint32), ("pos", np.float32, 3),
+                       ("dir", np.float32, 3), ("w", np.float32), ("t", np.float32)])
+assert EXIT_DTYPE.itemsize == ctypes.sizeof(McxExit) == 40
+
+# exported symbols and their signatures (restype, argtypes)
+_P = ctypes.c_void_p
+_u32, _u64, _i32, _f32, _f64 = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                 ctypes.c_float, ctypes.c_double)
+SIGNATURES = {
+    "mcx_abi_version": (_i32, []),
+    "mcx_status_string": (ctypes.c_char_p, [_i32]),
+    "mcx_run_cfg_default": (None, [ctypes.POINTER(McxRunCfg)]),
+    "mcx_create_volume": (_i32, [ctypes.POINTER(_P), _u32, _u32, _u32, _f32, _P, _i32]),
+    "mcx_update_labels": (_i32, [_P, _P, _i32]),
+    "mcx_set_media": (_i32, [_P, _u32, _P]),
+    "mcx_set_source": (_i32, [_P, _i32, _P, _P, _f32]),
+    "mcx_add_detector": (_i32, [_P, _P, _f32, ctypes.POINTER(_i32)]),
+    "mcx_clear_detectors": (_i32, [_P]),
+    "mcx_run": (_i32, [_P, ctypes.POINTER(McxRunCfg)]),
+    "mcx_sync": (_i32, [_P, _f64]),
+    "mcx_last_kernel_ms": (_i32, [_P, ctypes.POINTER(_f32)]),
+    "mcx_read_fluence": (_i32, [_P, _P, _u64, _i32, _i32]),
+    "mcx_detected_stride": (_i32, [_P]),
+    "mcx_read_detected": (_i32, [_P, _P, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "mcx_read_tally": (_i32, [_P, _P]),
+    "mcx_read_stats": (_i32, [_P, _P]),
+    "mcx_read_exits": (_i32, [_P, _P, _u64, ctypes.POINTER(_u64)]),
+    "mcx_launch_info": (_i32, [_P, _P]),
+    "mcx_last_error": (ctypes.c_char_p, [_P]),
+    "mcx_destroy": (None, [_P]),
+    "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
+    "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library.  Raises ImportError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1711_03244_gb300/build.py "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(sim, st: int):
+    if st != MCX_OK:
+        L = load()
+        msg = L.mcx_last_error(sim).decode() if L.mcx_last_error(sim) else ""
+        raise McxError(st, msg or L.mcx_status_string(st).decode())
+    return st
+
+
+def _ptr(x):
+    """data pointer of a NumPy array or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _on_device(x) -> int:
+    return int(bool(getattr(x, "is_cuda", False)))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------------ C-named API
+def mcx_run_cfg_default(**overrides) -> McxRunCfg:
+    cfg = McxRunCfg()
+    load().mcx_run_cfg_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "cuda_stream":
+            v = _stream_handle(v)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def mcx_create_volume(labels, voxel_mm: float):
+    """labels: uint8 [nz, ny, nx] NumPy array or torch tensor (host or CUDA)."""
+    L = load()
+    if hasattr(labels, "is_contiguous"):
+        assert labels.is_contiguous() and str(labels.dtype).endswith("uint8")
+        nz, ny, nx = labels.shape
+    else:
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        nz, ny, nx = labels.shape
+    h = ctypes.c_void_p()
+    _check(None, L.mcx_create_volume(ctypes.byref(h), nx, ny, nz, float(voxel_mm), _ptr(labels),
+                                     _on_device(labels)))
+    return h
+
+
+def mcx_update_labels(sim, labels):
+    if not hasattr(labels, "is_contiguous"):
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+    _check(sim, load().mcx_update_labels(sim, _ptr(labels), _on_device(labels)))
+
+
+def mcx_set_media(sim, props):
+    a = np.ascontiguousarray(props, dtype=np.float32).reshape(-1, 4)
+    _check(sim, load().mcx_set_media(sim, a.shape[0], _ptr(a)))
+
+
+def mcx_set_source(sim, kind: int, pos, direction, waist_mm: float = 0.0):
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    d = np.ascontiguousarray(direction, dtype=np.float32)
+    _check(sim, load().mcx_set_source(sim, int(kind), _ptr(p), _ptr(d), float(waist_mm)))
+
+
+def mcx_add_detector(sim, center, radius_mm: float) -> int:
+    c = np.ascontiguousarray(center, dtype=np.float32)
+    out = ctypes.c_int32()
+    _check(sim, load().mcx_add_detector(sim, _ptr(c), float(radius_mm), ctypes.byref(out)))
+    return out.value
+
+
+def mcx_clear_detectors(sim):
+    _check(sim, load().mcx_clear_detectors(sim))
+
+
+def mcx_run(sim, cfg: McxRunCfg):
+    _check(sim, load().mcx_run(sim, ctypes.byref(cfg)))
+
+
+def mcx_sync(sim, timeout_s: float = -1.0, allow_cap: bool = False) -> int:
+    st = load().mcx_sync(sim, float(timeout_s))
+    if st == MCX_E_CAP and allow_cap:
+        return st
+    return _check(sim, st)
+
+
+def mcx_last_kernel_ms(sim) -> float:
+    ms = ctypes.c_float()
+    _check(sim, load().mcx_last_kernel_ms(sim, ctypes.byref(ms)))
+    return ms.value
+
+
+def mcx_read_fluence(sim, dst, normalized: bool = False):
+    """dst: float32 NumPy array or torch tensor of n_gates*nz*ny*nx elements."""
+    n = dst.numel() if hasattr(dst, "numel") else dst.size
+    _check(sim, load().mcx_read_fluence(sim, _ptr(dst), n, int(normalized), _on_device(dst)))
+    return dst
+
+
+def mcx_detected_stride(sim) -> int:
+    return int(load().mcx_detected_stride(sim))
+
+
+def mcx_read_detected(sim, cap: Optional[int] = None) -> Tuple[np.ndarray, int]:
+    """Returns (records as uint32 words [n, stride], photons detected)."""
+    L = load()
+    stride = mcx_detected_stride(sim)
+    nw, nt = ctypes.c_uint64(), ctypes.c_uint64()
+    if cap is None:
+        _check(sim, L.mcx_read_detected(sim, None, 0, ctypes.byref(nw), ctypes.byref(nt)))
+        cap = int(nt.value)
+    buf = np.zeros((max(cap, 0), stride), dtype=np.uint32)
+    _check(sim, L.mcx_read_detected(sim, _ptr(buf) if cap else None, cap, ctypes.byref(nw),
+                                    ctypes.byref(nt)))
+    return buf[: nw.value], int(nt.value)
+
+
+def mcx_read_tally(sim) -> dict:
+    out = np.zeros(6, dtype=np.float64)
+    _check(sim, load().mcx_read_tally(sim, _ptr(out)))
+    return dict(zip(TALLY_NAMES, out.tolist()))
+
+
+def mcx_read_stats(sim) -> dict:
+    out = np.zeros(8, dtype=np.uint64)
+    _check(sim, load().mcx_read_stats(sim, _ptr(out)))
+    return dict(zip(STAT_NAMES, [int(v) for v in out]))
+
+
+def mcx_read_exits(sim, cap: int) -> np.ndarray:
+    buf = np.zeros(cap, dtype=EXIT_DTYPE)
+    nw = ctypes.c_uint64()
+    _check(sim, load().mcx_read_exits(sim, _ptr(buf) if cap else None, cap, ctypes.byref(nw)))
+    return buf[: nw.value]
+
+
+def mcx_launch_info(sim) -> dict:
+    out = np.zeros(4, dtype=np.int32)
+    _check(sim, load().mcx_launch_info(sim, _ptr(out)))
+    return dict(zip(("grid", "block", "blocks_per_sm", "regs"), out.tolist()))
+
+
+def mcx_last_error(sim=None) -> str:
+    r = load().mcx_last_error(sim)
+    return r.decode() if r else ""
+
+
+def mcx_destroy(sim):
+    if sim:
+        load().mcx_destroy(sim)
+
+
+def mcx_debug_uniforms(seed: int, photon: int, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float32)
+    _check(None, load().mcx_debug_uniforms(seed, photon, n, _ptr(out)))
+    return out
+
+
+def mcx_debug_primitive(kind: int, inputs: np.ndarray) -> np.ndarray:
+    a = np.ascontiguousarray(inputs, dtype=np.float32)
+    n = a.shape[0]
+    nout = {0: 2, 1: 3, 2: 1}[kind]
+    out = np.zeros((n, nout), dtype=np.float32)
+    _check(None, load().mcx_debug_primitive(kind, n, _ptr(a), _ptr(out)))
+    return out if nout > 1 else out[:, 0]
+
+
+def decode_detected(rec: np.ndarray) -> dict:
+    """Splits uint32 record words into named fields (see include/mcx.h)."""
+    f = rec.view(np.float32)
+    return {
+        "id": rec[:, 0].astype(np.uint64) | (rec[:, 1].astype(np.uint64) << np.uint64(32)),
+        "det": rec[:, 2].view(np.int32),
+        "nscat": rec[:, 3],
+        "w": f[:, 4],
+        "pos": f[:, 5:8],
+        "dir": f[:, 8:11],
+        "nrr": rec[:, 11],
+        "ppath": f[:, REC_BASE:],
+    }
+
+
+def photon_range(rank: int, world: int, n_per_rank: int) -> Tuple[int, int]:
+    """Photon-id range [offset, offset + n) of one rank when each of `world` ranks (one per
+    GPU) simulates its own n_per_rank photons.  Photons are independent and a run is a pure
+    function of (seed, id range), so the ranks' results compose into one run over
+    [0, world * n_per_rank) with no exchange during the walk."""
+    if not (0 <= rank < world) or n_per_rank < 0:
+        raise ValueError("need 0 <= rank < world and n_per_rank >= 0")
+    return rank * n_per_rank, n_per_rank
+
+
+# ------------------------------------------------------------------------ convenience
+class Simulation:
+    """Owns one mcx_sim handle; thin sugar over the C-named functions."""
+
+    def __init__(self, labels, voxel_mm: float, media, src_kind: int = 0,
+                 src_pos=(0.0, 0.0, 0.0), src_dir=(0.0, 0.0, 1.0), waist_mm: float = 0.0,
+                 detectors=None):
+        self.handle = mcx_create_volume(labels, voxel_mm)
+        self.shape = tuple(labels.shape)
+        mcx_set_media(self.handle, media)
+        mcx_set_source(self.handle, src_kind, src_pos, src_dir, waist_mm)
+        if detectors is not None:
+            for d in np.asarray(detectors, dtype=np.float64).reshape(-1, 4):
+                mcx_add_detector(self.handle, d[:3], d[3])
+        self.n_gates = 1
+
+    @classmethod
+    def from_workload(cls, wl):
+        return cls(wl.labels, wl.voxel_mm, wl.media, wl.src_kind, wl.src_pos, wl.src_dir,
+                   wl.waist_mm, wl.detectors if len(wl.detectors) else None)
+
+    def run(self, n_photons: int, n_gates: int = 1, dt_ns: float = 5.0, seed: int = 1,
+            stream=None, wait: bool = True, **kw):
+        cfg = mcx_run_cfg_default(n_photons=n_photons, n_gates=n_gates, dt_ns=dt_ns, seed=seed,
+                                  cuda_stream=stream, **kw)
+        self.n_gates = n_gates
+        mcx_run(self.handle, cfg)
+        if wait:
+            return mcx_sync(self.handle, allow_cap=True)
+        return MCX_OK
+
+    def fluence(self, normalized: bool = False, out=None):
+        if out is None:
+            out = np.zeros((self.n_gates,) + self.shape, dtype=np.float32)
+        return mcx_read_fluence(self.handle, out, normalized)
+
+    def tally(self):
+        return mcx_read_tally(self.handle)
+
+    def stats(self):
+        return mcx_read_stats(self.handle)
+
+    def exits(self, cap: int):
+        return mcx_read_exits(self.handle, cap)
+
+    def detected(self, cap=None):
+        rec, total = mcx_read_detected(self.handle, cap)
+        return decode_detected(rec), total
+
+    def kernel_ms(self) -> float:
+        return mcx_last_kernel_ms(self.handle)
+
+    def launch_info(self):
+        return mcx_launch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            mcx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,95 @@
+// Internal interface between the C-ABI layer (api.cu) and the photon-walk kernels
+// (walk.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mcx.h"
+
+namespace mcxg {
+
+constexpr int kMaxMedia = 256;       // label values 0..255
+constexpr int kMaxDetMedia = 33;     // media rows allowed when detectors are present
+constexpr int kMaxDet = 64;
+constexpr int kRecBase = 12;         // detected-record words before the partial paths
+constexpr int kClaimChunk = 32;      // photon ids a warp claims per global atomic
+constexpr float kC0 = 299.792458f;   // mm/ns
+
+// device status word bits
+constexpr unsigned kStatusCapped = 1u;
+constexpr unsigned kStatusDetOverflow = 2u;
+
+// Per-run constants in the walk's precision R.
+template <typename R>
+struct RunConsts {
+    R inv_dt;                         // 1 / gate width
+    R t_end;                          // n_gates * gate width, ns
+    R src_pos[3];                     // voxel units
+    R src_dir[3];                     // unit vector
+    R src_e1[3], src_e2[3];           // Gaussian launch-plane basis
+    R waist;                          // voxel units
+    R rr_threshold;
+    R rr_m;
+    R rr_inv_m;
+};
+
+struct WalkParams {
+    const uint8_t *labels;            // [nz][ny][nx]
+    float *fluence;                   // [n_gates][nvox] absorbed weight
+    const void *tab_a;                // [n_media] MedA<R>: mus, 1/mus, mua (voxel units), c0/(n h)
+    const void *tab_b;                // [n_media] MedB<R>: g, 1-g^2, 1+g^2, 1/(2g)
+    const void *tab_n;                // [n_media] R: refractive index
+    const void *tab_tpl;              // [n_media] R: ns per voxel length, n h / c0
+    const float4 *det;                // [n_det] cx, cy, cz, r^2 in voxel units
+    float *det_buf;                   // [max_detected][rec_stride] words
+    unsigned long long *det_count;
+    unsigned long long *photon_counter;
+    mcx_exit *exits;                  // [exit_log]
+    double *block_tally;              // [grid][MCX_NTALLY]
+    unsigned long long *block_stats;  // [grid][MCX_NSTAT]
+    unsigned *status;
+
+    int nx, ny, nz;
+    unsigned nvox;
+    int src_kind;
+    int n_media;
+    int n_det;
+    int rec_stride;
+    unsigned n_gates;
+    float h;                          // voxel edge, mm
+
+    // per-run constants, given in both precisions so the walk never converts in its loop
+    RunConsts<float> cf;
+    RunConsts<double> cd;
+
+    unsigned long long n_photons;
+    unsigned long long photon_offset;
+    unsigned long long seed;
+    unsigned long long max_detected;
+    unsigned long long exit_log;
+    unsigned long long max_events;
+    int reflect;
+};
+
+struct LaunchShape {
+    int grid, block, blocks_per_sm, regs;
+};
+
+// Walk precision: the FP32 product path, or the same kernel in FP64 (trajectory-parity
+// diagnostic; FP64 runs at a small fraction of the FP32 rate on this part).
+enum class Precision { F32 = 0, F64 = 1 };
+
+// walk.cu
+size_t walk_table_bytes(Precision prec, int n_media);   // bytes of the 4 tables together
+void walk_fill_tables(Precision prec, int n_media, const float *props, float h, void *host_buf,
+                      const void **tab_a_off, const void **tab_b_off, const void **tab_n_off,
+                      const void **tab_tpl_off);        // offsets into the buffer
+cudaError_t walk_query_shape(bool detectors, Precision prec, int block, int n_media, int n_det,
+                             LaunchShape *shape);
+cudaError_t walk_launch(const WalkParams &p, Precision prec, const LaunchShape &shape,
+                        cudaStream_t stream);
+cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out);
+cudaError_t debug_primitive(int kind, uint64_t n, const float *dev_in, float *dev_out);
+
+}  // namespace mcxg

@@ -1,0 +1,681 @@
+// Persistent photon-per-thread Monte Carlo walk through a labelled voxel volume (sm_103a).
+//
+// What one thread does per photon follows the photon simulation loop of the paper's
+// workflow (Fig. 1 paragraph) with the physics of its benchmark description (beside
+// Fig. 2): exponential hops in mean free paths, stepping voxel face to voxel face, Snell /
+// Fresnel at refractive-index mismatches (or termination at the exterior), Henyey-
+// Greenstein scattering with the MCML rotation, Russian roulette, race-free (atomic)
+// accumulation of absorbed weight into time gates, and disk detectors that record partial
+// path lengths.
+//
+// GB300-specific design (differs from the paper's OpenCL kernel):
+//  * Persistent grid (SMs x resident blocks).  A warp claims 32 photon ids with one global
+//    atomic and hands them to lanes as their photons finish, the per-warp analogue of the
+//    paper's in-workgroup dynamic load balancing (Fig. 3a paragraph) without a per-photon
+//    atomic.
+//  * Every photon's random stream derives from (seed, photon id), so a run is a pure
+//    function of (seed, id range) whatever the launch shape.
+//  * Position = integer voxel index + fraction inside the voxel: face distances are
+//    computed against 0 and 1, which keeps FP32 geometry at full precision anywhere in
+//    a large grid.
+//  * Absorbed weight is accumulated in a register while the photon stays in one
+//    (gate, voxel) and flushed with one fire-and-forget global atomic (RED.ADD.F32) when
+//    it leaves, instead of one atomic per segment.
+//  * Fast hardware math (MUFU ex2/lg2/sin/cos/rsqrt/rcp) in the FP32 path, the CUDA
+//    analogue of the paper's "native" math optimisation; the same kernel instantiated in
+//    FP64 serves as the trajectory-parity diagnostic.
+#include <cfloat>
+#include <cstdint>
+
+#include "mcx_internal.h"
+
+namespace mcxg {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+enum { EV_FACE = 0, EV_SCAT = 1, EV_TIME = 2 };
+
+// ------------------------------------------------------------------------------ math
+template <typename R> struct M;
+template <> struct M<float> {
+    static __device__ __forceinline__ float log(float x) { return __logf(x); }
+    static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+    static __device__ __forceinline__ void sincos_2pi(float x, float *s, float *c)
+    { __sincosf(6.28318530717958647692f * x, s, c); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float huge() { return FLT_MAX; }
+    static __device__ __forceinline__ float tiny_hop() { return 1e-12f; }
+};
+template <> struct M<double> {
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ void sincos_2pi(double x, double *s, double *c)
+    { ::sincospi(2.0 * x, s, c); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / ::sqrt(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double huge() { return DBL_MAX; }
+    static __device__ __forceinline__ double tiny_hop() { return 1e-300; }
+};
+
+// Per-label tables in the walk's precision.
+template <typename R> struct MedA { R mus, inv_mus, mua, len_per_t; };
+template <typename R> struct MedB { R one_m_g, one_p_g, one_m_g2, two_g; };
+
+// ------------------------------------------------------------------------------ RNG
+// SplitMix64 output k of `seed` (Steele, Lea & Flood 2014): state seed + k * golden gamma,
+// then the 64-bit finaliser.  Photon p's xorshift128+ state = outputs 2p+1 and 2p+2.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k)
+{
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct Rng {
+    uint64_t x, y;
+    __device__ __forceinline__ void seed(uint64_t s, uint64_t photon)
+    {
+        x = splitmix64(s, 2 * photon + 1);
+        y = splitmix64(s, 2 * photon + 2);
+        if ((x | y) == 0) y = 1;
+    }
+    // xorshift128+ (Vigna), shift triple 23/18/5; the top 23 bits k of the sum give the
+    // uniform (2k+1) 2^-24 in (0,1), exactly representable in float.
+    __device__ __forceinline__ float uniform()
+    {
+        uint64_t a = x;
+        const uint64_t b = y;
+        const uint64_t r = a + b;
+        x = b;
+        a ^= a << 23;
+        y = a ^ b ^ (a >> 18) ^ (b >> 5);
+        // (1 + k 2^-23) - (1 - 2^-24) = (2k + 1) 2^-24, both steps exact
+        const unsigned k = (unsigned)(r >> 41);
+        return __uint_as_float(0x3f800000u | k) - 0.99999994039535522461f;
+    }
+};
+
+// ------------------------------------------------------------------------------ physics
+// Henyey-Greenstein deflection by inverse CDF.  With D = 1 - g + 2 g xi and
+// f = (1 - g^2) / D, the textbook cosine is (1 + g^2 - f^2) / (2 g).  The same quantity is
+// produced here as the pair
+//     1 - cos = (1 - g)(1 - xi)(f + 1 - g) / D,    1 + cos = (1 + g) xi (1 + g + f) / D,
+// which follow from it by factoring f^2 - (1-g)^2 and (1+g)^2 - f^2; both are free of
+// cancellation, so sin^2 = (1 - cos)(1 + cos) keeps full FP32 precision for the small
+// deflections that dominate at g ~ 0.9 (1 - cos^2 would lose most of its bits there).
+// g = 0 reduces to the isotropic cos = 2 xi - 1 without a special case.
+template <typename R>
+__device__ __forceinline__ void hg_sample(const MedB<R> &B, R xi, R &ct, R &st)
+{
+    const R inv_d = R(1) / (B.one_m_g + B.two_g * xi);
+    const R f = B.one_m_g2 * inv_d;
+    const R omc = B.one_m_g * (R(1) - xi) * (f + B.one_m_g) * inv_d;
+    const R opc = B.one_p_g * xi * (B.one_p_g + f) * inv_d;
+    ct = R(0.5) * (opc - omc);
+    st = M<R>::sqrt(omc * opc);
+}
+
+// MCML rotation of unit vector u by deflection (cos ct, sin st) and azimuth (sp, cp).
+template <typename R>
+__device__ __forceinline__ void rotate(R &ux, R &uy, R &uz, R ct, R st, R sp, R cp)
+{
+    if (fabs(uz) > R(1) - R(1e-5)) {
+        ux = st * cp;
+        uy = st * sp;
+        uz = uz > R(0) ? ct : -ct;
+    } else {
+        // 1 - uz^2 evaluated as ux^2 + uy^2: no cancellation near the poles in FP32
+        const R one_m_uz2 = ux * ux + uy * uy;
+        const R rt = M<R>::rsqrt(one_m_uz2);          // 1 / sqrt(1 - uz^2)
+        const R a = st * rt;
+        const R nx = a * (ux * uz * cp - uy * sp) + ux * ct;
+        const R ny = a * (uy * uz * cp + ux * sp) + uy * ct;
+        const R nz = -st * cp * (one_m_uz2 * rt) + uz * ct;
+        ux = nx;
+        uy = ny;
+        uz = nz;
+    }
+}
+
+// Unpolarised Fresnel reflectance n1 -> n2 at incidence cosine ci, given sin^2 of the
+// transmission angle st2 < 1 (the caller handles total internal reflection).
+template <typename R>
+__device__ __forceinline__ R fresnel(R n1, R n2, R ci, R st2)
+{
+    const R ct = M<R>::sqrt(R(1) - st2);
+    const R rs = M<R>::div(n1 * ci - n2 * ct, n1 * ci + n2 * ct);
+    const R rp = M<R>::div(n1 * ct - n2 * ci, n1 * ct + n2 * ci);
+    return R(0.5) * (rs * rs + rp * rp);
+}
+
+template <typename R>
+__device__ __forceinline__ R inv_abs(R u)
+{
+    const R a = fabs(u);
+    return a > R(0) ? R(1) / a : M<R>::huge();
+}
+
+// ------------------------------------------------------------------------------ kernel
+// Dynamic shared memory, sized by the run's media and detector counts:
+//   double tally[8] | u64 stats[8] | MedA<R>[n_media] | MedB<R>[n_media] | R n[n_media] |
+//   R tpl[n_media] | float4 det[n_det]
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <typename R>
+struct SmemLayout {
+    size_t a, b, n, tpl, det, total;
+    __host__ __device__ SmemLayout(int n_media, int n_det)
+    {
+        a = 128;
+        b = align16(a + sizeof(MedA<R>) * n_media);
+        n = align16(b + sizeof(MedB<R>) * n_media);
+        tpl = align16(n + sizeof(R) * n_media);
+        det = align16(tpl + sizeof(R) * n_media);
+        total = align16(det + sizeof(float4) * n_det);
+    }
+};
+
+template <typename R> __device__ __forceinline__ const RunConsts<R> &consts(const WalkParams &p);
+template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(const WalkParams &p)
+{ return p.cf; }
+template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(const WalkParams &p)
+{ return p.cd; }
+
+template <typename R, bool DET>
+__global__ void __launch_bounds__(256)
+walk_kernel(const WalkParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SmemLayout<R> L(p.n_media, DET ? p.n_det : 0);
+    double *s_tally = reinterpret_cast<double *>(smem_raw);
+    unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem_raw + 64);
+    MedA<R> *s_a = reinterpret_cast<MedA<R> *>(smem_raw + L.a);
+    MedB<R> *s_b = reinterpret_cast<MedB<R> *>(smem_raw + L.b);
+    R *s_n = reinterpret_cast<R *>(smem_raw + L.n);
+    R *s_tpl = reinterpret_cast<R *>(smem_raw + L.tpl);
+    float4 *s_det = reinterpret_cast<float4 *>(smem_raw + L.det);
+
+    for (int i = threadIdx.x; i < p.n_media; i += blockDim.x) {
+        s_a[i] = static_cast<const MedA<R> *>(p.tab_a)[i];
+        s_b[i] = static_cast<const MedB<R> *>(p.tab_b)[i];
+        s_n[i] = static_cast<const R *>(p.tab_n)[i];
+        s_tpl[i] = static_cast<const R *>(p.tab_tpl)[i];
+    }
+    if (DET)
+        for (int i = threadIdx.x; i < p.n_det; i += blockDim.x) s_det[i] = p.det[i];
+    if (threadIdx.x < 8) s_tally[threadIdx.x] = 0.0;
+    if (threadIdx.x < 8) s_stats[threadIdx.x] = 0ull;
+    __syncthreads();
+
+    // per-run constants in the walk's precision (read from the parameter bank)
+    const RunConsts<R> &C = consts<R>(p);
+
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
+    const unsigned long long max_ev = p.max_events;
+
+    bool alive = false, done = false;
+    unsigned long long pid = 0;
+    Rng rng;
+    rng.x = rng.y = 0;
+    int ix = 0, iy = 0, iz = 0, lab = 0;
+    unsigned vlin = 0;
+    R qx = 0, qy = 0, qz = 0, ux = 0, uy = 0, uz = 1, iux = 0, iuy = 0, iuz = 0;
+    R w = 0, t = 0, s = 0, absorbed = 0, Lcur = 0;
+    R acc = 0;
+    unsigned long long acc_idx = ~0ull;
+    unsigned nscat = 0, nrr = 0, c_face = 0, c_fres = 0, c_flush = 0, c_rr = 0;
+    float Lpath[DET ? kMaxDetMedia : 1];
+
+    unsigned long long pool_next = 0;
+    unsigned pool_left = 0;
+
+    while (true) {
+        // ---- a1: claim photon ids for lanes without a photon (one atomic per 32 ids)
+        const unsigned need = __ballot_sync(kFull, !alive && !done);
+        if (need) {
+            const unsigned n = __popc(need);
+            const unsigned rank = __popc(need & lt_mask);
+            unsigned long long id;
+            if (pool_left >= n) {
+                id = pool_next + rank;
+                pool_next += n;
+                pool_left -= n;
+            } else {
+                unsigned long long nb = 0;
+                if (lane == 0) nb = atomicAdd(p.photon_counter, (unsigned long long)kClaimChunk);
+                nb = __shfl_sync(kFull, nb, 0);
+                id = rank < pool_left ? pool_next + rank : nb + (rank - pool_left);
+                const unsigned used_new = n - pool_left;
+                pool_next = nb + used_new;
+                pool_left = kClaimChunk - used_new;
+            }
+            if ((need >> lane) & 1u) {
+                if (id >= p.n_photons) {
+                    done = true;
+                } else {
+                    // ---- a2/a3: per-photon RNG and launch
+                    pid = p.photon_offset + id;
+                    rng.seed(p.seed, pid);
+                    R px = C.src_pos[0], py = C.src_pos[1], pz = C.src_pos[2];
+                    ux = C.src_dir[0]; uy = C.src_dir[1]; uz = C.src_dir[2];
+                    if (p.src_kind == 1) {
+                        const R xi1 = R(rng.uniform()), xi2 = R(rng.uniform());
+                        const R r = C.waist * M<R>::sqrt(-M<R>::log(xi1) * R(0.5));
+                        R sn, cs;
+                        M<R>::sincos_2pi(xi2, &sn, &cs);
+                        px += r * (cs * C.src_e1[0] + sn * C.src_e2[0]);
+                        py += r * (cs * C.src_e1[1] + sn * C.src_e2[1]);
+                        pz += r * (cs * C.src_e1[2] + sn * C.src_e2[2]);
+                    }
+                    const R fx = floor(px), fy = floor(py), fz = floor(pz);
+                    ix = (int)fx - ((px == fx && ux < R(0)) ? 1 : 0);
+                    iy = (int)fy - ((py == fy && uy < R(0)) ? 1 : 0);
+                    iz = (int)fz - ((pz == fz && uz < R(0)) ? 1 : 0);
+                    qx = px - R(ix); qy = py - R(iy); qz = pz - R(iz);
+                    iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
+                    w = R(1); t = R(0); s = R(0); absorbed = R(0); Lcur = R(0);
+                    nscat = nrr = c_face = c_fres = c_flush = c_rr = 0;
+                    acc = R(0);
+                    acc_idx = ~0ull;
+                    if (DET)
+                        for (int m = 0; m < p.n_media && m < kMaxDetMedia; ++m) Lpath[m] = 0.f;
+                    const bool inside = (unsigned)ix < (unsigned)p.nx &&
+                                        (unsigned)iy < (unsigned)p.ny &&
+                                        (unsigned)iz < (unsigned)p.nz;
+                    vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)p.nx + (unsigned)ix) : 0u;
+                    lab = inside ? (int)__ldg(p.labels + vlin) : 0;
+                    alive = true;
+                    if (lab == 0) {
+                        // launched outside the medium: counted as escaped, never enters
+                        alive = false;
+                        atomicAdd(&s_tally[MCX_TALLY_ESCAPED], 1.0);
+                        atomicAdd(&s_stats[MCX_STAT_PHOTONS], 1ull);
+                        const unsigned long long rel = pid - p.photon_offset;
+                        if (rel < p.exit_log) {
+                            mcx_exit e;
+                            e.fate = MCX_FATE_MISSED; e.nscat = 0;
+                            e.pos[0] = float(px * R(p.h)); e.pos[1] = float(py * R(p.h));
+                            e.pos[2] = float(pz * R(p.h));
+                            e.dir[0] = float(ux); e.dir[1] = float(uy); e.dir[2] = float(uz);
+                            e.w = 1.f; e.t = 0.f;
+                            p.exits[rel] = e;
+                        }
+                    }
+                }
+            }
+        }
+        if (__all_sync(kFull, done)) break;
+        if (!alive) continue;
+
+        int fate = MCX_FATE_NONE;
+        if ((unsigned long long)nscat + c_face >= max_ev) {
+            fate = MCX_FATE_CAPPED;
+        } else {
+            // ---- a4: new hop when the last one is used up
+            if (s <= R(0)) {
+                s = -M<R>::log(R(rng.uniform()));
+                s = s > M<R>::tiny_hop() ? s : M<R>::tiny_hop();
+            }
+            const MedA<R> A = s_a[lab];
+            // ---- a5: nearest face (lowest axis on ties), scattering point, time limit
+            // (a fraction that rounding pushed past its face gives a zero-length step)
+            const R dxf = fmax((ux >= R(0) ? R(1) - qx : qx) * iux, R(0));
+            const R dyf = fmax((uy >= R(0) ? R(1) - qy : qy) * iuy, R(0));
+            const R dzf = fmax((uz >= R(0) ? R(1) - qz : qz) * iuz, R(0));
+            R l = dxf;
+            int ax = 0;
+            if (dyf < l) { l = dyf; ax = 1; }
+            if (dzf < l) { l = dzf; ax = 2; }
+            int ev = EV_FACE;
+            const R dscat = s * A.inv_mus;
+            if (dscat <= l) { l = dscat; ev = EV_SCAT; }
+            R dtime = (C.t_end - t) * A.len_per_t;
+            dtime = dtime > R(0) ? dtime : R(0);
+            if (dtime <= l) { l = dtime; ev = EV_TIME; }
+
+            // ---- a7: gate of the segment start; a6: absorb and accumulate
+            unsigned gate = (unsigned)(t * C.inv_dt);
+            gate = gate < p.n_gates ? gate : p.n_gates - 1u;
+            const unsigned long long idx = (unsigned long long)gate * p.nvox + vlin;
+            qx += l * ux;
+            qy += l * uy;
+            qz += l * uz;
+            t += l * s_tpl[lab];
+            s = ev == EV_SCAT ? R(0) : s - l * A.mus;
+            if (DET) Lcur += l;
+            const R wn = w * M<R>::exp(-A.mua * l);
+            const R dw = w - wn;
+            w = wn;
+            absorbed += dw;
+            if (idx != acc_idx) {
+                if (acc != R(0)) {
+                    atomicAdd(p.fluence + acc_idx, float(acc));
+                    ++c_flush;
+                }
+                acc = R(0);
+                acc_idx = idx;
+            }
+            acc += dw;
+
+            if (ev == EV_TIME) {
+                fate = MCX_FATE_TIME;
+            } else if (ev == EV_FACE) {
+                // ---- a8: voxel face
+                ++c_face;
+                const R ua = ax == 0 ? ux : (ax == 1 ? uy : uz);
+                const bool up = ua >= R(0);
+                const R qb = up ? R(1) : R(0);
+                const int ia = (ax == 0 ? ix : (ax == 1 ? iy : iz)) + (up ? 1 : -1);
+                const int dim = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
+                const unsigned stride = ax == 0 ? 1u : (ax == 1 ? (unsigned)p.nx : nxy);
+                const unsigned nlin = up ? vlin + stride : vlin - stride;
+                const bool inside = (unsigned)ia < (unsigned)dim;
+                const int b = inside ? (int)__ldg(p.labels + nlin) : 0;
+                // photon on the face
+                qx = ax == 0 ? qb : qx;
+                qy = ax == 1 ? qb : qy;
+                qz = ax == 2 ? qb : qz;
+                bool enter = false, escape = false;
+                if (b == lab) {
+                    enter = true;
+                } else if (!p.reflect) {
+                    // the paper's B1: the exterior terminates, internal mismatches pass
+                    if (b == 0) escape = true; else enter = true;
+                } else {
+                    const R na = s_n[lab], nb = s_n[b];
+                    if (na == nb) {
+                        if (b == 0) escape = true; else enter = true;
+                    } else {
+                        ++c_fres;
+                        const R ci = fabs(ua);
+                        const R eta = M<R>::div(na, nb);
+                        const R st2 = eta * eta * (R(1) - ci * ci);
+                        bool refl = true;                 // total internal reflection
+                        if (st2 < R(1)) refl = R(rng.uniform()) < fresnel(na, nb, ci, st2);
+                        if (refl) {
+                            ux = ax == 0 ? -ux : ux;
+                            uy = ax == 1 ? -uy : uy;
+                            uz = ax == 2 ? -uz : uz;
+                        } else {
+                            // Snell: tangential components x eta, normal = +-cos(theta_t)
+                            const R ctt = M<R>::sqrt(R(1) - st2);
+                            const R un = up ? ctt : -ctt;
+                            ux = ax == 0 ? un : ux * eta;
+                            uy = ax == 1 ? un : uy * eta;
+                            uz = ax == 2 ? un : uz * eta;
+                            iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
+                            if (b == 0) escape = true; else enter = true;
+                        }
+                    }
+                }
+                if (enter) {
+                    ix = ax == 0 ? ia : ix;
+                    iy = ax == 1 ? ia : iy;
+                    iz = ax == 2 ? ia : iz;
+                    qx = ax == 0 ? R(1) - qb : qx;
+                    qy = ax == 1 ? R(1) - qb : qy;
+                    qz = ax == 2 ? R(1) - qb : qz;
+                    vlin = nlin;
+                    if (DET && b != lab) {
+                        if (lab < kMaxDetMedia) Lpath[lab] += float(Lcur);
+                        Lcur = R(0);
+                    }
+                    lab = b;
+                }
+                if (escape) fate = MCX_FATE_ESCAPED;
+            } else {
+                // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
+                ++nscat;
+                const MedB<R> B = s_b[lab];
+                R ct, st;
+                hg_sample(B, R(rng.uniform()), ct, st);
+                R sn, cs;
+                M<R>::sincos_2pi(R(rng.uniform()), &sn, &cs);
+                rotate(ux, uy, uz, ct, st, sn, cs);
+                iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
+                if (w < C.rr_threshold) {
+                    ++c_rr;
+                    if (R(rng.uniform()) < C.rr_inv_m) {
+                        atomicAdd(&s_tally[MCX_TALLY_RR_GAINED], double((C.rr_m - R(1)) * w));
+                        w *= C.rr_m;
+                        ++nrr;
+                    } else {
+                        fate = MCX_FATE_ROULETTE;
+                    }
+                }
+            }
+        }
+        if (fate == MCX_FATE_NONE) continue;
+
+        // ---- photon finished: flush the deposit run, tallies, logs, detectors (a9, a12)
+        if (acc != R(0)) {
+            atomicAdd(p.fluence + acc_idx, float(acc));
+            ++c_flush;
+        }
+        const int slot = fate == MCX_FATE_ESCAPED ? MCX_TALLY_ESCAPED
+                       : (fate == MCX_FATE_ROULETTE ? MCX_TALLY_RR_KILLED : MCX_TALLY_TIME);
+        atomicAdd(&s_tally[slot], double(w));
+        atomicAdd(&s_tally[MCX_TALLY_ABSORBED], double(absorbed));
+        atomicAdd(&s_stats[MCX_STAT_SCATTER], (unsigned long long)nscat);
+        atomicAdd(&s_stats[MCX_STAT_FACE], (unsigned long long)c_face);
+        atomicAdd(&s_stats[MCX_STAT_FRESNEL], (unsigned long long)c_fres);
+        atomicAdd(&s_stats[MCX_STAT_FLUSH], (unsigned long long)c_flush);
+        atomicAdd(&s_stats[MCX_STAT_ROULETTE], (unsigned long long)c_rr);
+        atomicAdd(&s_stats[MCX_STAT_PHOTONS], 1ull);
+        if (fate == MCX_FATE_CAPPED) {
+            atomicAdd(&s_stats[MCX_STAT_CAPPED], 1ull);
+            atomicOr(p.status, kStatusCapped);
+        }
+        const R hh = R(p.h);
+        const R ex = (R(ix) + qx) * hh, ey = (R(iy) + qy) * hh, ez = (R(iz) + qz) * hh;
+        const unsigned long long rel = pid - p.photon_offset;
+        if (rel < p.exit_log) {
+            mcx_exit e;
+            e.fate = fate; e.nscat = nscat;
+            e.pos[0] = float(ex); e.pos[1] = float(ey); e.pos[2] = float(ez);
+            e.dir[0] = float(ux); e.dir[1] = float(uy); e.dir[2] = float(uz);
+            e.w = float(w); e.t = float(t);
+            p.exits[rel] = e;
+        }
+        if (DET && fate == MCX_FATE_ESCAPED) {
+            const float vx = float(R(ix) + qx), vy = float(R(iy) + qy), vz = float(R(iz) + qz);
+            for (int d = 0; d < p.n_det; ++d) {
+                const float4 D = s_det[d];
+                const float dx = vx - D.x, dy = vy - D.y, dz = vz - D.z;
+                if (dx * dx + dy * dy + dz * dz <= D.w) {
+                    atomicAdd(&s_stats[MCX_STAT_DETECTED], 1ull);
+                    const unsigned long long slot_i = atomicAdd(p.det_count, 1ull);
+                    if (slot_i < p.max_detected) {
+                        if (lab < kMaxDetMedia) Lpath[lab] += float(Lcur);
+                        float *rec = p.det_buf + slot_i * (unsigned long long)p.rec_stride;
+                        rec[0] = __uint_as_float((unsigned)(pid & 0xffffffffull));
+                        rec[1] = __uint_as_float((unsigned)(pid >> 32));
+                        rec[2] = __int_as_float(d);
+                        rec[3] = __uint_as_float(nscat);
+                        rec[4] = float(w);
+                        rec[5] = float(ex); rec[6] = float(ey); rec[7] = float(ez);
+                        rec[8] = float(ux); rec[9] = float(uy); rec[10] = float(uz);
+                        rec[11] = __uint_as_float(nrr);
+                        for (int m = 1; m < p.n_media && m < kMaxDetMedia; ++m)
+                            rec[kRecBase + m - 1] = Lpath[m] * p.h;
+                    } else {
+                        atomicOr(p.status, kStatusDetOverflow);
+                    }
+                    break;
+                }
+            }
+        }
+        alive = false;
+    }
+
+    __syncthreads();
+    if (threadIdx.x < MCX_NTALLY)
+        p.block_tally[(size_t)blockIdx.x * MCX_NTALLY + threadIdx.x] = s_tally[threadIdx.x];
+    if (threadIdx.x < MCX_NSTAT)
+        p.block_stats[(size_t)blockIdx.x * MCX_NSTAT + threadIdx.x] = s_stats[threadIdx.x];
+}
+
+// ------------------------------------------------------------------------------ debug
+__global__ void uniforms_kernel(uint64_t seed, uint64_t photon, uint64_t n, float *out)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    Rng r;
+    r.seed(seed, photon);
+    for (uint64_t i = 0; i < n; ++i) out[i] = r.uniform();
+}
+
+__global__ void primitive_kernel(int kind, uint64_t n, const float *in, float *out)
+{
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (kind == 0) {
+        const float g = in[2 * i], xi = in[2 * i + 1];
+        MedB<float> B;
+        B.one_m_g = 1.f - g; B.one_p_g = 1.f + g; B.one_m_g2 = 1.f - g * g; B.two_g = 2.f * g;
+        float ct, st;
+        hg_sample(B, xi, ct, st);
+        out[2 * i] = ct;
+        out[2 * i + 1] = st;
+    } else if (kind == 1) {
+        float ux = in[6 * i], uy = in[6 * i + 1], uz = in[6 * i + 2];
+        float sn, cs;
+        M<float>::sincos_2pi(in[6 * i + 5], &sn, &cs);
+        rotate(ux, uy, uz, in[6 * i + 3], in[6 * i + 4], sn, cs);
+        out[3 * i] = ux; out[3 * i + 1] = uy; out[3 * i + 2] = uz;
+    } else {
+        const float n1 = in[3 * i], n2 = in[3 * i + 1], ci = in[3 * i + 2];
+        const float eta = M<float>::div(n1, n2);
+        const float st2 = eta * eta * (1.f - ci * ci);
+        out[i] = st2 < 1.f ? fresnel(n1, n2, ci, st2) : 1.f;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ host side
+namespace {
+template <typename R>
+size_t table_bytes(int n_media)
+{
+    return align16(sizeof(MedA<R>) * n_media) + align16(sizeof(MedB<R>) * n_media) +
+           align16(sizeof(R) * n_media) * 2;
+}
+
+// Per-label constants in voxel units (h = voxel edge): mus h, 1/(mus h), mua h, c0/(n h),
+// the HG constants, n, and n h / c0.  Set-up arithmetic on the inputs, done once per run.
+template <typename R>
+void fill(int n_media, const float *props, float h, unsigned char *buf, const void **oa,
+          const void **ob, const void **on, const void **ot)
+{
+    const size_t a = 0, b = align16(sizeof(MedA<R>) * n_media);
+    const size_t n = b + align16(sizeof(MedB<R>) * n_media);
+    const size_t t = n + align16(sizeof(R) * n_media);
+    const R hh = R(h), c0 = R(299.792458);
+    for (int m = 0; m < n_media; ++m) {
+        const R mua = R(props[4 * m]), mus = R(props[4 * m + 1]);
+        const R g = R(props[4 * m + 2]), nn = R(props[4 * m + 3]);
+        MedA<R> A;
+        A.mus = mus * hh;
+        A.inv_mus = A.mus > R(0) ? R(1) / A.mus : R(INFINITY);
+        A.mua = mua * hh;
+        A.len_per_t = c0 / (nn * hh);
+        MedB<R> B;
+        B.one_m_g = R(1) - g;
+        B.one_p_g = R(1) + g;
+        B.one_m_g2 = R(1) - g * g;
+        B.two_g = R(2) * g;
+        reinterpret_cast<MedA<R> *>(buf + a)[m] = A;
+        reinterpret_cast<MedB<R> *>(buf + b)[m] = B;
+        reinterpret_cast<R *>(buf + n)[m] = nn;
+        reinterpret_cast<R *>(buf + t)[m] = nn * hh / c0;
+    }
+    *oa = (const void *)a;
+    *ob = (const void *)b;
+    *on = (const void *)n;
+    *ot = (const void *)t;
+}
+
+template <typename R, bool DET>
+cudaError_t shape_for(int block, int n_media, int n_det, LaunchShape *shape)
+{
+    const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0).total;
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET>, block,
+                                                           smem)) != cudaSuccess)
+        return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET>)) != cudaSuccess) return e;
+    shape->block = block;
+    shape->blocks_per_sm = per_sm;
+    shape->grid = sms * (per_sm > 0 ? per_sm : 1);
+    shape->regs = fa.numRegs;
+    return cudaSuccess;
+}
+
+template <typename R, bool DET>
+cudaError_t launch(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
+{
+    const size_t smem = SmemLayout<R>(p.n_media, DET ? p.n_det : 0).total;
+    walk_kernel<R, DET><<<s.grid, s.block, smem, st>>>(p);
+    return cudaGetLastError();
+}
+}  // namespace
+
+size_t walk_table_bytes(Precision prec, int n_media)
+{
+    return prec == Precision::F64 ? table_bytes<double>(n_media) : table_bytes<float>(n_media);
+}
+
+void walk_fill_tables(Precision prec, int n_media, const float *props, float h, void *host_buf,
+                      const void **oa, const void **ob, const void **on, const void **ot)
+{
+    unsigned char *b = static_cast<unsigned char *>(host_buf);
+    if (prec == Precision::F64) fill<double>(n_media, props, h, b, oa, ob, on, ot);
+    else fill<float>(n_media, props, h, b, oa, ob, on, ot);
+}
+
+cudaError_t walk_query_shape(bool det, Precision prec, int block, int n_media, int n_det,
+                             LaunchShape *shape)
+{
+    if (prec == Precision::F64)
+        return det ? shape_for<double, true>(block, n_media, n_det, shape)
+                   : shape_for<double, false>(block, n_media, n_det, shape);
+    return det ? shape_for<float, true>(block, n_media, n_det, shape)
+               : shape_for<float, false>(block, n_media, n_det, shape);
+}
+
+cudaError_t walk_launch(const WalkParams &p, Precision prec, const LaunchShape &s,
+                        cudaStream_t st)
+{
+    const bool det = p.n_det > 0;
+    if (prec == Precision::F64) return det ? launch<double, true>(p, s, st) : launch<double, false>(p, s, st);
+    return det ? launch<float, true>(p, s, st) : launch<float, false>(p, s, st);
+}
+
+cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out)
+{
+    uniforms_kernel<<<1, 1>>>(seed, photon, n, dev_out);
+    return cudaGetLastError();
+}
+
+cudaError_t debug_primitive(int kind, uint64_t n, const float *dev_in, float *dev_out)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    primitive_kernel<<<blocks, 256>>>(kind, n, dev_in, dev_out);
+    return cudaGetLastError();
+}
+
+}  // namespace mcxg
