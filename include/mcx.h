@@ -188,6 +188,38 @@ mcx_status mcx_launch_info(mcx_sim *sim, int32_t out[4]);
 const char *mcx_last_error(const mcx_sim *sim);
 void mcx_destroy(mcx_sim *sim);
 
+/* ---- allocation-free run --------------------------------------------------------------
+   The paper has no counterpart to this entry point; it exists for callers that cannot let
+   a library allocate device memory: applications whose own pool or caching allocator owns
+   the whole device memory (memory taken behind its back is invisible to it and fragments
+   it), and latency-sensitive loops that cannot afford the device-wide synchronisation a
+   cudaFree may cause.
+
+   Runs one simulation like mcx_create_volume + set_media + set_source + mcx_run, on the
+   caller's buffers, and calls no cudaMalloc, cudaFree or other allocating routine.
+     labels_dev   uint8 [nz][ny][nx] on the current device (read only)
+     props        host float [n_media][4] as in mcx_set_media; 1 <= n_media <= 32
+     src_kind, pos_mm, dir, waist_mm   as in mcx_set_source
+     cfg          as for mcx_run (cuda_stream honoured); needs precision = 0, exit_log = 0,
+                  max_detected = 0 (no detectors), grid_size <= 2048
+     fluence_dev  float [n_gates][nz][ny][nx] on the current device; zeroed, then filled
+                  with absorbed weight (as mcx_read_fluence with normalized = 0)
+     tally_dev    double [MCX_NTALLY] on the current device, receives the energy tallies
+   Its working memory (photon counter, status, per-label tables, per-block partials) is a
+   fixed 226 KiB array in the library, held by every GPU that loads it until the process
+   exits; sizes beyond its limits are rejected with MCX_E_ARG.  The first call on a device
+   looks up that array's device address; make that first call before any stream capture.
+   The call checks the labels (a 4-byte read-back that waits for the stream), then enqueues
+   the rest on cfg->cuda_stream and returns.  Every call reuses the same array: calls
+   whose work overlaps on one GPU (other streams or host threads) race on it; serialise
+   them.  Errors: MCX_E_ARG / MCX_E_STATE (a label >= n_media) / MCX_E_CUDA, described by
+   mcx_last_error(NULL). */
+mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, uint32_t nz,
+                           float voxel_mm, uint32_t n_media, const float *props,
+                           int32_t src_kind, const float pos_mm[3], const float dir[3],
+                           float waist_mm, const mcx_run_cfg *cfg, float *fluence_dev,
+                           double *tally_dev);
+
 /* ---- diagnostics: run the library's device primitives on small host arrays ---------- */
 
 /* First n uniforms of photon `photon`'s stream for `seed`, as the walk kernel draws them. */

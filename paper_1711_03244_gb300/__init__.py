@@ -96,6 +96,8 @@ SIGNATURES = {
     "mcx_launch_info": (_i32, [_P, _P]),
     "mcx_last_error": (ctypes.c_char_p, [_P]),
     "mcx_destroy": (None, [_P]),
+    "mcx_run_noalloc": (_i32, [_P, _u32, _u32, _u32, _f32, _u32, _P, _i32, _P, _P, _f32,
+                               ctypes.POINTER(McxRunCfg), _P, _P]),
     "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
     "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
 }
@@ -278,6 +280,20 @@ def mcx_last_error(sim=None) -> str:
 def mcx_destroy(sim):
     if sim:
         load().mcx_destroy(sim)
+
+
+def mcx_run_noalloc(labels_dev, voxel_mm: float, media, src_kind: int, pos, direction,
+                    waist_mm: float, cfg: McxRunCfg, fluence_dev, tally_dev):
+    """Allocation-free run on caller-owned device tensors (see include/mcx.h): labels_dev
+    uint8 [nz, ny, nx], fluence_dev float32 [n_gates, nz, ny, nx], tally_dev float64 [6],
+    all on the current CUDA device.  Enqueued on cfg.cuda_stream."""
+    nz, ny, nx = labels_dev.shape
+    a = np.ascontiguousarray(media, dtype=np.float32).reshape(-1, 4)
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    d = np.ascontiguousarray(direction, dtype=np.float32)
+    _check(None, load().mcx_run_noalloc(_ptr(labels_dev), nx, ny, nz, float(voxel_mm), a.shape[0],
+                                        _ptr(a), int(src_kind), _ptr(p), _ptr(d), float(waist_mm),
+                                        ctypes.byref(cfg), _ptr(fluence_dev), _ptr(tally_dev)))
 
 
 def mcx_debug_uniforms(seed: int, photon: int, n: int) -> np.ndarray:

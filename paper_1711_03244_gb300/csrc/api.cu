@@ -205,6 +205,8 @@ struct mcx_sim {
     std::string err;
 };
 
+void mcxg::set_global_error(const std::string &msg) { g_err = msg; }
+
 static mcx_status fail(mcx_sim *s, mcx_status st, const std::string &msg)
 {
     if (s) s->err = msg; else g_err = msg;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/mcx.h"
@@ -89,6 +90,9 @@ cudaError_t walk_query_shape(bool detectors, Precision prec, int block, int n_me
                              LaunchShape *shape);
 cudaError_t walk_launch(const WalkParams &p, Precision prec, const LaunchShape &shape,
                         cudaStream_t stream);
+// api.cu: the error text mcx_last_error(NULL) returns (per host thread)
+void set_global_error(const std::string &msg);
+
 cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out);
 cudaError_t debug_primitive(int kind, uint64_t n, const float *dev_in, float *dev_out);
 
