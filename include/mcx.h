@@ -222,7 +222,9 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
 
 /* ---- diagnostics: run the library's device primitives on small host arrays ---------- */
 
-/* First n uniforms of photon `photon`'s stream for `seed`, as the walk kernel draws them. */
+/* Photon `photon`'s stream for `seed`, as the walk kernel draws it: for each of the first
+   n generator outputs, out_host[2i] is the single-uniform draw (top 23 bits) and
+   out_host[2i+1] the second uniform of a pair draw (bits 40..18); 2n floats. */
 mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *out_host);
 
 /* Evaluates one device primitive on n input tuples (host arrays, row-major):

@@ -116,6 +116,9 @@ def lib():
         L.orc_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                    ctypes.c_void_p]
         L.orc_uniforms.restype = None
+        L.orc_uniform_pairs.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_void_p]
+        L.orc_uniform_pairs.restype = None
         L.orc_hg_cos.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_hg_cos.restype = ctypes.c_double
         L.orc_rotate.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
@@ -138,6 +141,13 @@ def uniforms(seed: int, photon: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.float64)
     lib().orc_uniforms(seed, photon, n, out.ctypes.data)
     return out
+
+
+def uniform_pairs(seed: int, photon: int, n: int) -> np.ndarray:
+    """n pair draws (two uniforms from one generator output each), shape [n, 2]."""
+    out = np.empty(2 * n, dtype=np.float64)
+    lib().orc_uniform_pairs(seed, photon, n, out.ctypes.data)
+    return out.reshape(n, 2)
 
 
 def hg_cos(g: float, xi: float) -> float:

@@ -31,8 +31,11 @@
  * Random numbers.  Each photon has its own xorshift128+ stream (Vigna, "Further
  * scramblings of Marsaglia's xorshift generators", shifts 23/18/5), seeded from the
  * SplitMix64 sequence of the run seed (Steele, Lea & Flood 2014): photon p takes outputs
- * number 2p+1 and 2p+2.  This is the per-thread independent seeding of the paper's
- * workflow, made per photon so a run is a pure function of (seed, photon ids).
+ * number 2p+1 and 2p+2.  Events that need one uniform (hop, Fresnel, roulette) take the
+ * top 23 bits of one output; events that need two (Gaussian launch point, scattering)
+ * take the top 23 bits and bits 40..18 of one output.  This is the per-thread
+ * independent seeding of the paper's workflow, made per photon so a run is a pure
+ * function of (seed, photon ids).
  * ---------------------------------------------------------------------------------- */
 static uint64_t sm64_mix(uint64_t z)
 {
@@ -74,11 +77,28 @@ static double rng_uniform(orc_rng *g)
     return (double)(2 * k + 1) * (1.0 / 16777216.0);
 }
 
+/* two uniforms from one output, for events that need two (Gaussian launch point,
+   scattering): the top 23 bits give the first and bits 40..18 the second, each as
+   (2k+1) 2^-24 */
+static void rng_uniform_pair(orc_rng *g, double *u1, double *u2)
+{
+    const uint64_t r = rng_next(g);
+    *u1 = (double)(2 * (r >> 41) + 1) * (1.0 / 16777216.0);
+    *u2 = (double)(2 * ((r >> 18) & 0x7FFFFFULL) + 1) * (1.0 / 16777216.0);
+}
+
 void orc_uniforms(uint64_t seed, uint64_t photon, uint64_t n, double *out)
 {
     orc_rng g;
     rng_init(&g, seed, photon);
     for (uint64_t i = 0; i < n; ++i) out[i] = rng_uniform(&g);
+}
+
+void orc_uniform_pairs(uint64_t seed, uint64_t photon, uint64_t n, double *out)
+{
+    orc_rng g;
+    rng_init(&g, seed, photon);
+    for (uint64_t i = 0; i < n; ++i) rng_uniform_pair(&g, &out[2 * i], &out[2 * i + 1]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -211,7 +231,8 @@ static void run_photon(const orc_problem *P, uint64_t id, orc_ctx *C, orc_exit *
         /* I(r) ~ exp(-2 r^2 / w^2): r = w sqrt(-ln xi1 / 2), phi = 2 pi xi2, in the plane
            normal to the beam spanned by e1 = normalise(dir x z) (x when the beam is along
            z) and e2 = dir x e1. */
-        const double xi1 = rng_uniform(&rng), xi2 = rng_uniform(&rng);
+        double xi1, xi2;
+        rng_uniform_pair(&rng, &xi1, &xi2);
         const double r = P->waist * sqrt(-log(xi1) / 2.0), ph = 2.0 * ORC_PI * xi2;
         double e1[3], e2[3];
         if (fabs(dir[2]) > 0.999999) { e1[0] = 1; e1[1] = 0; e1[2] = 0; }
@@ -349,8 +370,10 @@ static void run_photon(const orc_problem *P, uint64_t id, orc_ctx *C, orc_exit *
         } else {                             /* scattering event */
             C->count[ORC_C_SCATTER]++;
             ++nscat;
-            const double ct = orc_hg_cos(g, rng_uniform(&rng));
-            const double ph = 2.0 * ORC_PI * rng_uniform(&rng);
+            double xi_hg, xi_phi;
+            rng_uniform_pair(&rng, &xi_hg, &xi_phi);
+            const double ct = orc_hg_cos(g, xi_hg);
+            const double ph = 2.0 * ORC_PI * xi_phi;
             double nd[3];
             orc_rotate(dir, ct, ph, nd);
             dir[0] = nd[0]; dir[1] = nd[1]; dir[2] = nd[2];

@@ -497,6 +497,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.h = s->h;
     {
         RunConsts<double> &d = p.cd;
+        d.dt = (double)cfg->dt_ns;
         d.inv_dt = 1.0 / (double)cfg->dt_ns;
         d.t_end = (double)cfg->dt_ns * cfg->n_gates;
         for (int a = 0; a < 3; ++a) {
@@ -521,6 +522,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
         d.rr_m = cfg->rr_m;
         d.rr_inv_m = cfg->rr_threshold > 0.f ? 1.0 / (double)cfg->rr_m : 0.0;
         RunConsts<float> &f = p.cf;
+        f.dt = cfg->dt_ns;
         f.inv_dt = (float)d.inv_dt;
         f.t_end = (float)d.t_end;
         for (int a = 0; a < 3; ++a) {
@@ -772,10 +774,10 @@ mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float 
     if (!out_host && n) return fail(nullptr, MCX_E_ARG, "out is NULL");
     if (n == 0) return MCX_OK;
     float *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, n * sizeof(float));
+    cudaError_t e = cudaMalloc(&d, 2 * n * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "allocating");
     e = debug_uniforms(seed, photon, n, d);
-    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, 2 * n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e == cudaSuccess ? MCX_OK : cuda_fail(nullptr, e, "debug uniforms");
 }

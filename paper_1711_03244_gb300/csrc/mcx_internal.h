@@ -24,6 +24,7 @@ constexpr unsigned kStatusDetOverflow = 2u;
 // Per-run constants in the walk's precision R.
 template <typename R>
 struct RunConsts {
+    R dt;                             // gate width, ns
     R inv_dt;                         // 1 / gate width
     R t_end;                          // n_gates * gate width, ns
     R src_pos[3];                     // voxel units

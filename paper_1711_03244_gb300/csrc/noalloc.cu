@@ -223,6 +223,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.n_gates = cfg->n_gates;
     p.h = voxel_mm;
     RunConsts<float> &c = p.cf;
+    c.dt = cfg->dt_ns;
     c.inv_dt = (float)(1.0 / (double)cfg->dt_ns);
     c.t_end = (float)((double)cfg->dt_ns * cfg->n_gates);
     double d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn}, e1[3];

@@ -83,9 +83,22 @@ struct Rng {
         y = splitmix64(s, 2 * photon + 2);
         if ((x | y) == 0) y = 1;
     }
-    // xorshift128+ (Vigna), shift triple 23/18/5; the top 23 bits k of the sum give the
-    // uniform (2k+1) 2^-24 in (0,1), exactly representable in float.
+    // xorshift128+ (Vigna), shift triple 23/18/5; one uniform (hop, Fresnel, roulette) is
+    // (2k+1) 2^-24 from the top 23 bits k of one output, exactly representable in float.
     __device__ __forceinline__ float uniform()
+    {
+        const uint64_t r = next();
+        return from_bits((unsigned)(r >> 41));
+    }
+    // Two uniforms from one output (Gaussian launch point, scattering): the top 23 bits
+    // and bits 40..18.
+    __device__ __forceinline__ void pair(float &u1, float &u2)
+    {
+        const uint64_t r = next();
+        u1 = from_bits((unsigned)(r >> 41));
+        u2 = from_bits((unsigned)(r >> 18) & 0x7fffffu);
+    }
+    __device__ __forceinline__ uint64_t next()
     {
         uint64_t a = x;
         const uint64_t b = y;
@@ -93,8 +106,11 @@ struct Rng {
         x = b;
         a ^= a << 23;
         y = a ^ b ^ (a >> 18) ^ (b >> 5);
-        // (1 + k 2^-23) - (1 - 2^-24) = (2k + 1) 2^-24, both steps exact
-        const unsigned k = (unsigned)(r >> 41);
+        return r;
+    }
+    // (1 + k 2^-23) - (1 - 2^-24) = (2k + 1) 2^-24, both steps exact
+    static __device__ __forceinline__ float from_bits(unsigned k)
+    {
         return __uint_as_float(0x3f800000u | k) - 0.99999994039535522461f;
     }
 };
@@ -152,11 +168,21 @@ __device__ __forceinline__ R fresnel(R n1, R n2, R ci, R st2)
     return R(0.5) * (rs * rs + rp * rp);
 }
 
+// Signed reciprocal of a direction component, +huge for 0.  With it the distance to the
+// face ahead along that axis is one FMA on the in-voxel fraction q:
+//   u > 0: (1 - q) / u = fma(q, -inv, inv);   u < 0: -q / u = fma(q, -inv, 0)
+// i.e. fma(q, -inv, max(inv, 0)); u = 0 gives huge * (1 - q), never the nearest face.
 template <typename R>
-__device__ __forceinline__ R inv_abs(R u)
+__device__ __forceinline__ R inv_dir(R u)
 {
-    const R a = fabs(u);
-    return a > R(0) ? R(1) / a : M<R>::huge();
+    return u != R(0) ? R(1) / u : M<R>::huge();
+}
+
+template <typename R>
+__device__ __forceinline__ R face_dist(R q, R inv)
+{
+    const R d = fma(q, -inv, inv > R(0) ? inv : R(0));
+    return d > R(0) ? d : R(0);
 }
 
 // ------------------------------------------------------------------------------ kernel
@@ -217,7 +243,7 @@ walk_kernel(const WalkParams p)
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
-    const unsigned long long max_ev = p.max_events;
+    const unsigned max_ev = p.max_events < 0xffffffffull ? (unsigned)p.max_events : 0xffffffffu;
 
     bool alive = false, done = false;
     unsigned long long pid = 0;
@@ -226,108 +252,130 @@ walk_kernel(const WalkParams p)
     int ix = 0, iy = 0, iz = 0, lab = 0;
     unsigned vlin = 0;
     R qx = 0, qy = 0, qz = 0, ux = 0, uy = 0, uz = 1, iux = 0, iuy = 0, iuz = 0;
-    R w = 0, t = 0, s = 0, absorbed = 0, Lcur = 0;
-    R acc = 0;
-    unsigned long long acc_idx = ~0ull;
+    R w = 0, t = 0, s = 0, absorbed = 0, Lcur = 0, acc = 0;
+    unsigned gate = 0;            // time gate of the current deposit run
+    R t_next = 0;                 // time at which the gate advances
     unsigned nscat = 0, nrr = 0, c_face = 0, c_fres = 0, c_flush = 0, c_rr = 0;
     float Lpath[DET ? kMaxDetMedia : 1];
 
     unsigned long long pool_next = 0;
     unsigned pool_left = 0;
+    const unsigned last_gate = p.n_gates - 1u;
+
+    // a12 (per run): one atomic per (gate, voxel) run of deposits
+    auto flush = [&]() {
+        if (acc != R(0)) {
+            atomicAdd(p.fluence + (unsigned long long)gate * p.nvox + vlin, float(acc));
+            ++c_flush;
+        }
+        acc = R(0);
+    };
+    // a4: dimensionless hop in mean free paths
+    auto new_hop = [&]() {
+        const R h = -M<R>::log(R(rng.uniform()));
+        s = h > M<R>::tiny_hop() ? h : M<R>::tiny_hop();
+    };
 
     while (true) {
-        // ---- a1: claim photon ids for lanes without a photon (one atomic per 32 ids)
-        const unsigned need = __ballot_sync(kFull, !alive && !done);
-        if (need) {
-            const unsigned n = __popc(need);
-            const unsigned rank = __popc(need & lt_mask);
-            unsigned long long id;
-            if (pool_left >= n) {
-                id = pool_next + rank;
-                pool_next += n;
-                pool_left -= n;
-            } else {
-                unsigned long long nb = 0;
-                if (lane == 0) nb = atomicAdd(p.photon_counter, (unsigned long long)kClaimChunk);
-                nb = __shfl_sync(kFull, nb, 0);
-                id = rank < pool_left ? pool_next + rank : nb + (rank - pool_left);
-                const unsigned used_new = n - pool_left;
-                pool_next = nb + used_new;
-                pool_left = kClaimChunk - used_new;
-            }
-            if ((need >> lane) & 1u) {
-                if (id >= p.n_photons) {
-                    done = true;
+        if (__any_sync(kFull, !alive)) {
+            // ---- a1: claim photon ids for lanes without a photon (one atomic per 32 ids)
+            const unsigned need = __ballot_sync(kFull, !alive && !done);
+            if (need) {
+                const unsigned n = __popc(need);
+                const unsigned rank = __popc(need & lt_mask);
+                unsigned long long id;
+                if (pool_left >= n) {
+                    id = pool_next + rank;
+                    pool_next += n;
+                    pool_left -= n;
                 } else {
-                    // ---- a2/a3: per-photon RNG and launch
-                    pid = p.photon_offset + id;
-                    rng.seed(p.seed, pid);
-                    R px = C.src_pos[0], py = C.src_pos[1], pz = C.src_pos[2];
-                    ux = C.src_dir[0]; uy = C.src_dir[1]; uz = C.src_dir[2];
-                    if (p.src_kind == 1) {
-                        const R xi1 = R(rng.uniform()), xi2 = R(rng.uniform());
-                        const R r = C.waist * M<R>::sqrt(-M<R>::log(xi1) * R(0.5));
-                        R sn, cs;
-                        M<R>::sincos_2pi(xi2, &sn, &cs);
-                        px += r * (cs * C.src_e1[0] + sn * C.src_e2[0]);
-                        py += r * (cs * C.src_e1[1] + sn * C.src_e2[1]);
-                        pz += r * (cs * C.src_e1[2] + sn * C.src_e2[2]);
-                    }
-                    const R fx = floor(px), fy = floor(py), fz = floor(pz);
-                    ix = (int)fx - ((px == fx && ux < R(0)) ? 1 : 0);
-                    iy = (int)fy - ((py == fy && uy < R(0)) ? 1 : 0);
-                    iz = (int)fz - ((pz == fz && uz < R(0)) ? 1 : 0);
-                    qx = px - R(ix); qy = py - R(iy); qz = pz - R(iz);
-                    iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
-                    w = R(1); t = R(0); s = R(0); absorbed = R(0); Lcur = R(0);
-                    nscat = nrr = c_face = c_fres = c_flush = c_rr = 0;
-                    acc = R(0);
-                    acc_idx = ~0ull;
-                    if (DET)
-                        for (int m = 0; m < p.n_media && m < kMaxDetMedia; ++m) Lpath[m] = 0.f;
-                    const bool inside = (unsigned)ix < (unsigned)p.nx &&
-                                        (unsigned)iy < (unsigned)p.ny &&
-                                        (unsigned)iz < (unsigned)p.nz;
-                    vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)p.nx + (unsigned)ix) : 0u;
-                    lab = inside ? (int)__ldg(p.labels + vlin) : 0;
-                    alive = true;
-                    if (lab == 0) {
-                        // launched outside the medium: counted as escaped, never enters
-                        alive = false;
-                        atomicAdd(&s_tally[MCX_TALLY_ESCAPED], 1.0);
-                        atomicAdd(&s_stats[MCX_STAT_PHOTONS], 1ull);
-                        const unsigned long long rel = pid - p.photon_offset;
-                        if (rel < p.exit_log) {
-                            mcx_exit e;
-                            e.fate = MCX_FATE_MISSED; e.nscat = 0;
-                            e.pos[0] = float(px * R(p.h)); e.pos[1] = float(py * R(p.h));
-                            e.pos[2] = float(pz * R(p.h));
-                            e.dir[0] = float(ux); e.dir[1] = float(uy); e.dir[2] = float(uz);
-                            e.w = 1.f; e.t = 0.f;
-                            p.exits[rel] = e;
+                    unsigned long long nb = 0;
+                    if (lane == 0) nb = atomicAdd(p.photon_counter, (unsigned long long)kClaimChunk);
+                    nb = __shfl_sync(kFull, nb, 0);
+                    id = rank < pool_left ? pool_next + rank : nb + (rank - pool_left);
+                    const unsigned used_new = n - pool_left;
+                    pool_next = nb + used_new;
+                    pool_left = kClaimChunk - used_new;
+                }
+                if ((need >> lane) & 1u) {
+                    if (id >= p.n_photons) {
+                        done = true;
+                    } else {
+                        // ---- a2/a3: per-photon RNG and launch
+                        pid = p.photon_offset + id;
+                        rng.seed(p.seed, pid);
+                        R px = C.src_pos[0], py = C.src_pos[1], pz = C.src_pos[2];
+                        ux = C.src_dir[0]; uy = C.src_dir[1]; uz = C.src_dir[2];
+                        if (p.src_kind == 1) {
+                            float f1, f2;
+                            rng.pair(f1, f2);
+                            const R r = C.waist * M<R>::sqrt(-M<R>::log(R(f1)) * R(0.5));
+                            R sn, cs;
+                            M<R>::sincos_2pi(R(f2), &sn, &cs);
+                            px += r * (cs * C.src_e1[0] + sn * C.src_e2[0]);
+                            py += r * (cs * C.src_e1[1] + sn * C.src_e2[1]);
+                            pz += r * (cs * C.src_e1[2] + sn * C.src_e2[2]);
+                        }
+                        const R fx = floor(px), fy = floor(py), fz = floor(pz);
+                        ix = (int)fx - ((px == fx && ux < R(0)) ? 1 : 0);
+                        iy = (int)fy - ((py == fy && uy < R(0)) ? 1 : 0);
+                        iz = (int)fz - ((pz == fz && uz < R(0)) ? 1 : 0);
+                        qx = px - R(ix); qy = py - R(iy); qz = pz - R(iz);
+                        iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
+                        w = R(1); t = R(0); absorbed = R(0); Lcur = R(0); acc = R(0);
+                        gate = 0;
+                        t_next = last_gate > 0 ? C.dt : M<R>::huge();
+                        nscat = nrr = c_face = c_fres = c_flush = c_rr = 0;
+                        if (DET)
+                            for (int m = 0; m < p.n_media && m < kMaxDetMedia; ++m) Lpath[m] = 0.f;
+                        const bool inside = (unsigned)ix < (unsigned)p.nx &&
+                                            (unsigned)iy < (unsigned)p.ny &&
+                                            (unsigned)iz < (unsigned)p.nz;
+                        vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)p.nx + (unsigned)ix) : 0u;
+                        lab = inside ? (int)__ldg(p.labels + vlin) : 0;
+                        alive = lab != 0;
+                        if (alive) {
+                            new_hop();
+                        } else {
+                            // launched outside the medium: counted as escaped, never enters
+                            atomicAdd(&s_tally[MCX_TALLY_ESCAPED], 1.0);
+                            atomicAdd(&s_stats[MCX_STAT_PHOTONS], 1ull);
+                            const unsigned long long rel = pid - p.photon_offset;
+                            if (rel < p.exit_log) {
+                                mcx_exit e;
+                                e.fate = MCX_FATE_MISSED; e.nscat = 0;
+                                e.pos[0] = float(px * R(p.h)); e.pos[1] = float(py * R(p.h));
+                                e.pos[2] = float(pz * R(p.h));
+                                e.dir[0] = float(ux); e.dir[1] = float(uy); e.dir[2] = float(uz);
+                                e.w = 1.f; e.t = 0.f;
+                                p.exits[rel] = e;
+                            }
                         }
                     }
                 }
             }
+            if (__all_sync(kFull, done)) break;
+            if (!alive) continue;
         }
-        if (__all_sync(kFull, done)) break;
-        if (!alive) continue;
 
         int fate = MCX_FATE_NONE;
-        if ((unsigned long long)nscat + c_face >= max_ev) {
+        if (nscat + c_face >= max_ev) {
             fate = MCX_FATE_CAPPED;
         } else {
-            // ---- a4: new hop when the last one is used up
-            if (s <= R(0)) {
-                s = -M<R>::log(R(rng.uniform()));
-                s = s > M<R>::tiny_hop() ? s : M<R>::tiny_hop();
+            // ---- a7: the gate of this segment's start (time only increases)
+            if (t >= t_next) {
+                flush();
+                unsigned g2 = (unsigned)(t * C.inv_dt);
+                g2 = g2 > gate + 1u ? g2 : gate + 1u;
+                gate = g2 < last_gate ? g2 : last_gate;
+                t_next = gate < last_gate ? R(gate + 1u) * C.dt : M<R>::huge();
             }
             const MedA<R> A = s_a[lab];
             // ---- a5: nearest face (lowest axis on ties), scattering point, time limit
             // (a fraction that rounding pushed past its face gives a zero-length step)
-            const R dxf = fmax((ux >= R(0) ? R(1) - qx : qx) * iux, R(0));
-            const R dyf = fmax((uy >= R(0) ? R(1) - qy : qy) * iuy, R(0));
-            const R dzf = fmax((uz >= R(0) ? R(1) - qz : qz) * iuz, R(0));
+            const R dxf = face_dist(qx, iux);
+            const R dyf = face_dist(qy, iuy);
+            const R dzf = face_dist(qz, iuz);
             R l = dxf;
             int ax = 0;
             if (dyf < l) { l = dyf; ax = 1; }
@@ -339,10 +387,7 @@ walk_kernel(const WalkParams p)
             dtime = dtime > R(0) ? dtime : R(0);
             if (dtime <= l) { l = dtime; ev = EV_TIME; }
 
-            // ---- a7: gate of the segment start; a6: absorb and accumulate
-            unsigned gate = (unsigned)(t * C.inv_dt);
-            gate = gate < p.n_gates ? gate : p.n_gates - 1u;
-            const unsigned long long idx = (unsigned long long)gate * p.nvox + vlin;
+            // ---- a5/a6: move, age, absorb into the current (gate, voxel) run
             qx += l * ux;
             qy += l * uy;
             qz += l * uz;
@@ -353,14 +398,6 @@ walk_kernel(const WalkParams p)
             const R dw = w - wn;
             w = wn;
             absorbed += dw;
-            if (idx != acc_idx) {
-                if (acc != R(0)) {
-                    atomicAdd(p.fluence + acc_idx, float(acc));
-                    ++c_flush;
-                }
-                acc = R(0);
-                acc_idx = idx;
-            }
             acc += dw;
 
             if (ev == EV_TIME) {
@@ -402,6 +439,9 @@ walk_kernel(const WalkParams p)
                             ux = ax == 0 ? -ux : ux;
                             uy = ax == 1 ? -uy : uy;
                             uz = ax == 2 ? -uz : uz;
+                            iux = ax == 0 ? -iux : iux;
+                            iuy = ax == 1 ? -iuy : iuy;
+                            iuz = ax == 2 ? -iuz : iuz;
                         } else {
                             // Snell: tangential components x eta, normal = +-cos(theta_t)
                             const R ctt = M<R>::sqrt(R(1) - st2);
@@ -409,12 +449,13 @@ walk_kernel(const WalkParams p)
                             ux = ax == 0 ? un : ux * eta;
                             uy = ax == 1 ? un : uy * eta;
                             uz = ax == 2 ? un : uz * eta;
-                            iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
+                            iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
                             if (b == 0) escape = true; else enter = true;
                         }
                     }
                 }
                 if (enter) {
+                    flush();                              // the deposit run ends with the voxel
                     ix = ax == 0 ? ia : ix;
                     iy = ax == 1 ? ia : iy;
                     iz = ax == 2 ? ia : iz;
@@ -429,16 +470,19 @@ walk_kernel(const WalkParams p)
                     lab = b;
                 }
                 if (escape) fate = MCX_FATE_ESCAPED;
+                else if (s <= R(0)) new_hop();            // hop used up by rounding at the face
             } else {
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
                 const MedB<R> B = s_b[lab];
+                float xi_hg, xi_phi;
+                rng.pair(xi_hg, xi_phi);
                 R ct, st;
-                hg_sample(B, R(rng.uniform()), ct, st);
+                hg_sample(B, R(xi_hg), ct, st);
                 R sn, cs;
-                M<R>::sincos_2pi(R(rng.uniform()), &sn, &cs);
+                M<R>::sincos_2pi(R(xi_phi), &sn, &cs);
                 rotate(ux, uy, uz, ct, st, sn, cs);
-                iux = inv_abs(ux); iuy = inv_abs(uy); iuz = inv_abs(uz);
+                iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
                 if (w < C.rr_threshold) {
                     ++c_rr;
                     if (R(rng.uniform()) < C.rr_inv_m) {
@@ -449,15 +493,13 @@ walk_kernel(const WalkParams p)
                         fate = MCX_FATE_ROULETTE;
                     }
                 }
+                if (fate == MCX_FATE_NONE) new_hop();     // a4: the next hop
             }
         }
         if (fate == MCX_FATE_NONE) continue;
 
         // ---- photon finished: flush the deposit run, tallies, logs, detectors (a9, a12)
-        if (acc != R(0)) {
-            atomicAdd(p.fluence + acc_idx, float(acc));
-            ++c_flush;
-        }
+        flush();
         const int slot = fate == MCX_FATE_ESCAPED ? MCX_TALLY_ESCAPED
                        : (fate == MCX_FATE_ROULETTE ? MCX_TALLY_RR_KILLED : MCX_TALLY_TIME);
         atomicAdd(&s_tally[slot], double(w));
@@ -527,7 +569,7 @@ __global__ void uniforms_kernel(uint64_t seed, uint64_t photon, uint64_t n, floa
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     Rng r;
     r.seed(seed, photon);
-    for (uint64_t i = 0; i < n; ++i) out[i] = r.uniform();
+    for (uint64_t i = 0; i < n; ++i) r.pair(out[2 * i], out[2 * i + 1]);
 }
 
 __global__ void primitive_kernel(int kind, uint64_t n, const float *in, float *out)

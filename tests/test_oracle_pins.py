@@ -49,6 +49,24 @@ def test_uniforms_range_grid_and_moments(orc):
     assert abs(r) < 5 / math.sqrt(n)
 
 
+def test_uniform_pairs_split_one_output(orc):
+    """A pair draw consumes one generator output: its first value equals the single draw
+    at the same position, its second comes from lower bits of the same output and is
+    itself uniform and uncorrelated with the first."""
+    single = orc.uniforms(99, 3, 20_000)
+    pairs = orc.uniform_pairs(99, 3, 20_000)
+    assert np.array_equal(pairs[:, 0], single)
+    lo = pairs[:, 1]
+    k = lo * 2 ** 24
+    assert np.all(k == np.round(k)) and np.all(np.round(k) % 2 == 1)
+    n = lo.size
+    assert abs(lo.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+    assert abs(np.corrcoef(pairs[:, 0], lo)[0, 1]) < 5 / math.sqrt(n)
+    hist, _ = np.histogram(lo, bins=32, range=(0, 1))
+    chi2 = ((hist - n / 32) ** 2 / (n / 32)).sum()
+    assert chi2 < 31 + 6 * math.sqrt(2 * 31)
+
+
 def test_uniform_streams_independent_per_photon(orc):
     a = orc.uniforms(7, 0, 2000)
     b = orc.uniforms(7, 1, 2000)
