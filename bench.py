@@ -80,7 +80,7 @@ def walk_traffic():
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     text = open(prof).read()
-    m_h = re.search(r"walk\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_h = re.search(r"walk\.cu sha256\[:16\][^:\n]*:\s*([0-9a-f]{16})", text)
     m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
     if m_h and m_b and m_h.group(1) == h:
         return float(m_b.group(1))
@@ -194,6 +194,8 @@ def main():
     ap.add_argument("--cpu-photons", type=int, default=50_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-model", action="store_true",
+                    help="skip the pilot runs of the linear runtime model T = a n + T0")
     args = ap.parse_args()
 
     world, rank, local = dist_env()
@@ -268,7 +270,7 @@ def main():
     flu_pinned = torch.empty((wl.n_gates,) + wl.labels.shape, dtype=torch.float32).pin_memory()
     e2e_times = []
     h2d = d2h = 0
-    for k in range(args.e2e_steps + 1):
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mcx.mcx_update_labels(sim.handle, labels_pinned.numpy())
@@ -283,8 +285,40 @@ def main():
             e2e_times.append(dt)
         h2d = wl.labels.nbytes + wl.media.astype(np.float32).nbytes
         d2h = flu_pinned.numel() * 4 + 6 * 8 + rec.nbytes
-    e2e_ms = 1e3 * float(np.mean(e2e_times))
-    e2e_val = world * n / e2e_ms
+    e2e_ms = 1e3 * float(np.mean(e2e_times)) if e2e_times else float("nan")
+    e2e_val = world * n / e2e_ms if e2e_times else None
+
+    # ---- the paper's linear runtime model T = a n + T0 from pilot runs at 1e6 and 5e6
+    # photons (device time of one complete run, and host wall time of create + run + read)
+    model = None
+    if not args.no_model:
+        def pilot(npil):
+            cfgp = mcx.mcx_run_cfg_default(n_photons=npil, photon_offset=offset,
+                                           n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=wl.seed,
+                                           max_detected=wl.max_detected, cuda_stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with mcx.Simulation.from_workload(wl) as s2:
+                s2.n_gates = wl.n_gates
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mcx.mcx_run(s2.handle, cfgp)
+                e1.record(stream)
+                mcx.mcx_sync(s2.handle, allow_cap=True)
+                s2.fluence()
+                s2.tally()
+                s2.detected()
+            wall_ms = 1e3 * (time.perf_counter() - t0)
+            return e0.elapsed_time(e1), wall_ms
+        pilot(1_000_000)                                  # warm the path once
+        d1, w1 = pilot(1_000_000)
+        d2, w2 = pilot(5_000_000)
+        a_dev = (d2 - d1) / 4e6
+        a_wall = (w2 - w1) / 4e6
+        model = {"n1": 1_000_000, "n2": 5_000_000,
+                 "device": {"a_ns_per_photon": a_dev * 1e6, "T0_ms": d1 - a_dev * 1e6},
+                 "wall": {"a_ns_per_photon": a_wall * 1e6, "T0_ms": w1 - a_wall * 1e6}}
 
     # ---- roofline of the walk kernel: algorithmic thread-ops / launch time vs issue peak
     pk = peaks()
@@ -311,6 +345,7 @@ def main():
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps},
+            "runtime_model": model,
             "events": {k: int(v) for k, v in stats.items()},
             "energy_balance_rel": abs(tally["absorbed"] + tally["escaped"] +
                                       tally["time_exceeded"] + tally["roulette_killed"] -
