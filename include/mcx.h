@@ -82,13 +82,28 @@ typedef struct mcx_run_cfg {
     uint64_t max_detected;         /* capacity of the detected-photon buffer (records) */
     uint64_t exit_log;             /* log fate/exit of photons offset .. offset+exit_log-1 */
     uint64_t max_events_per_photon;/* segment cap per photon (0 = library default 1e8) */
-    int32_t accum_mode;            /* 0: FP32 register run-length + global FP32 atomics */
+    int32_t accum_mode;            /* fluence accumulation; every mode first sums a photon's
+                                      deposits in a register while it stays in one (gate, voxel):
+                                      0: one FP32 atomic add per run into the map (fastest);
+                                      1: compensated FP32 pairs: runs inside the block tile (below)
+                                         go to a block-private shared-memory (hi, lo) pair, the
+                                         rounding error of each hi addition recovered exactly
+                                         (TwoSum on the atomic's old value) into lo; each block
+                                         flushes its tile once, in FP64, into the tile's FP64 map;
+                                         runs outside the tile go to a global (hi, lo) pair the
+                                         same way; the result is hi + lo + tile;
+                                      2: FP64 global atomics (a diagnostic that isolates
+                                         accumulation error; FP64 is slow on this part) */
     int32_t block_size;            /* threads per block, multiple of 32 (0 = 256) */
     int32_t grid_size;             /* persistent blocks (0 = SMs x resident blocks/SM) */
     int32_t precision;             /* 0: FP32 photon state (the product path); 1: the same walk
                                       in FP64, a trajectory-parity diagnostic that runs at the
                                       part's much lower FP64 rate */
     void *cuda_stream;             /* cudaStream_t to enqueue on (NULL = legacy default) */
+    int32_t tile_lo[4];            /* accum_mode 1: block tile origin (voxel x, y, z, gate) */
+    int32_t tile_size[4];          /* and extent; all zero = automatic: 16 x 16 x 24 voxels of
+                                      gate 0 from the source voxel down, clipped to the grid;
+                                      at most 6144 (gate, voxel) entries (48 KiB per block) */
 } mcx_run_cfg;
 
 /* Fate and end state of one logged photon (fixed-seed parity log). */
@@ -156,6 +171,11 @@ mcx_status mcx_last_kernel_ms(mcx_sim *sim, float *ms);
    n_gates*nx*ny*nz. */
 mcx_status mcx_read_fluence(mcx_sim *sim, float *dst, uint64_t n_elems, int32_t normalized,
                             int32_t dst_on_device);
+
+/* As mcx_read_fluence, in FP64: the map as accumulated (accum_mode 1: hi + lo + tile
+   summed in FP64; accum_mode 2: the FP64 map; accum_mode 0: the FP32 map widened). */
+mcx_status mcx_read_fluence64(mcx_sim *sim, double *dst, uint64_t n_elems, int32_t normalized,
+                              int32_t dst_on_device);
 
 /* Words (4 bytes each) per detected-photon record: 12 + (n_media - 1). */
 int32_t mcx_detected_stride(const mcx_sim *sim);

@@ -57,6 +57,8 @@ class McxRunCfg(ctypes.Structure):
         ("grid_size", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
+        ("tile_lo", ctypes.c_int32 * 4),
+        ("tile_size", ctypes.c_int32 * 4),
     ]
 
 
@@ -88,6 +90,7 @@ SIGNATURES = {
     "mcx_sync": (_i32, [_P, _f64]),
     "mcx_last_kernel_ms": (_i32, [_P, ctypes.POINTER(_f32)]),
     "mcx_read_fluence": (_i32, [_P, _P, _u64, _i32, _i32]),
+    "mcx_read_fluence64": (_i32, [_P, _P, _u64, _i32, _i32]),
     "mcx_detected_stride": (_i32, [_P]),
     "mcx_read_detected": (_i32, [_P, _P, _u64, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "mcx_read_tally": (_i32, [_P, _P]),
@@ -158,6 +161,8 @@ def mcx_run_cfg_default(**overrides) -> McxRunCfg:
     for k, v in overrides.items():
         if k == "cuda_stream":
             v = _stream_handle(v)
+        if k in ("tile_lo", "tile_size"):
+            v = (ctypes.c_int32 * 4)(*v)
         setattr(cfg, k, v)
     return cfg
 
@@ -226,6 +231,13 @@ def mcx_read_fluence(sim, dst, normalized: bool = False):
     """dst: float32 NumPy array or torch tensor of n_gates*nz*ny*nx elements."""
     n = dst.numel() if hasattr(dst, "numel") else dst.size
     _check(sim, load().mcx_read_fluence(sim, _ptr(dst), n, int(normalized), _on_device(dst)))
+    return dst
+
+
+def mcx_read_fluence64(sim, dst, normalized: bool = False):
+    """dst: float64 NumPy array or torch tensor of n_gates*nz*ny*nx elements."""
+    n = dst.numel() if hasattr(dst, "numel") else dst.size
+    _check(sim, load().mcx_read_fluence64(sim, _ptr(dst), n, int(normalized), _on_device(dst)))
     return dst
 
 
@@ -372,6 +384,11 @@ class Simulation:
         if out is None:
             out = np.zeros((self.n_gates,) + self.shape, dtype=np.float32)
         return mcx_read_fluence(self.handle, out, normalized)
+
+    def fluence64(self, normalized: bool = False, out=None):
+        if out is None:
+            out = np.zeros((self.n_gates,) + self.shape, dtype=np.float64)
+        return mcx_read_fluence64(self.handle, out, normalized)
 
     def tally(self):
         return mcx_read_tally(self.handle)

@@ -104,15 +104,45 @@ __global__ void finalize_kernel(const double *bt, const unsigned long long *bs, 
     }
 }
 
-// fluence rate per launched photon: E * inv_norm[label], inv_norm = 1 / (mua h^3 N dt)
-__global__ void normalize_kernel(const float *E, const uint8_t *labels, const float *inv_norm,
-                                 float *out, unsigned nvox, unsigned n_gates)
+// The fluence map as accumulated, in the caller's type, optionally normalised to fluence
+// rate per launched photon (x inv_norm[label], inv_norm = 1 / (mua h^3 N dt)):
+//   accum 0: the FP32 map;  accum 2: the FP64 map;
+//   accum 1: hi + lo (+ the tile's FP64 sum inside the block tile), summed in FP64.
+struct TileBox {
+    int lo[4], size[4];
+};
+
+template <typename T>
+__global__ void resolve_kernel(int mode, const float *hi, const float *lo, const double *f64,
+                               TileBox tb, unsigned nx, unsigned ny, unsigned nvox,
+                               unsigned n_gates, const uint8_t *labels, const float *inv_norm,
+                               T *out)
 {
     const size_t total = (size_t)nvox * n_gates;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += stride) {
         const unsigned v = (unsigned)(i % nvox);
-        out[i] = E[i] * inv_norm[labels[v]];
+        if (mode == 0) {
+            float f = hi[i];
+            if (inv_norm) f *= inv_norm[labels[v]];
+            out[i] = (T)f;
+            continue;
+        }
+        double d;
+        if (mode == 2) {
+            d = f64[i];
+        } else {
+            d = (double)hi[i] + (double)lo[i];
+            const unsigned g = (unsigned)(i / nvox);
+            const unsigned x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+            const unsigned tx = x - (unsigned)tb.lo[0], ty = y - (unsigned)tb.lo[1];
+            const unsigned tz = z - (unsigned)tb.lo[2], tg = g - (unsigned)tb.lo[3];
+            if (tx < (unsigned)tb.size[0] && ty < (unsigned)tb.size[1] &&
+                tz < (unsigned)tb.size[2] && tg < (unsigned)tb.size[3])
+                d += f64[((tg * tb.size[2] + tz) * tb.size[1] + ty) * tb.size[0] + tx];
+        }
+        if (inv_norm) d *= (double)inv_norm[labels[v]];
+        out[i] = (T)d;
     }
 }
 
@@ -189,8 +219,9 @@ struct mcx_sim {
     bool source_set = false;
     std::vector<float> det;             // [n_det][4] cx, cy, cz, r (mm)
 
-    DevBuf labels, fluence, tables, detb, det_buf, exits, block_tally, block_stats, ctrl, out,
-        staging, inv_norm, sort_keys, sort_vals;
+    DevBuf labels, fluence, fluence_lo, fluence64, tables, detb, det_buf, exits, block_tally,
+        block_stats, ctrl, out, staging, inv_norm, sort_keys, sort_vals;
+    int tile_lo[4] = {0, 0, 0, 0}, tile_size[4] = {0, 0, 0, 0};
     std::vector<unsigned char> host_tables;
 
     // last run
@@ -200,7 +231,7 @@ struct mcx_sim {
     int rec_stride = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_done = nullptr;
-    std::map<std::tuple<int, int, int, int, int>, LaunchShape> shape_cache;
+    std::map<std::tuple<int, int, int, int, int, int, int>, LaunchShape> shape_cache;
 
     std::string err;
 };
@@ -418,7 +449,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     if (cfg->photon_offset + cfg->n_photons < cfg->photon_offset)
         return fail(s, MCX_E_ARG, "photon id range overflows");
     if (cfg->precision != 0 && cfg->precision != 1) return fail(s, MCX_E_ARG, "precision is 0 or 1");
-    if (cfg->accum_mode != 0) return fail(s, MCX_E_ARG, "accum_mode must be 0");
+    if (cfg->accum_mode < 0 || cfg->accum_mode > 2) return fail(s, MCX_E_ARG, "accum_mode is 0, 1 or 2");
     const int block = cfg->block_size ? cfg->block_size : 256;
     if (block < 32 || block > 256 || block % 32) return fail(s, MCX_E_ARG, "block_size: 32..256, multiple of 32");
     if (cfg->grid_size < 0) return fail(s, MCX_E_ARG, "grid_size < 0");
@@ -428,11 +459,45 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     if (s->ran) MCX_CUDA(s, cudaEventSynchronize(s->ev_done), "waiting for the previous run");
 
     const Precision prec = cfg->precision ? Precision::F64 : Precision::F32;
-    const auto key = std::make_tuple((int)(n_det > 0), (int)prec, block, (int)s->n_media, n_det);
+    const int accum = cfg->accum_mode;
+    // block tile of the compensated mode: given, or 16 x 16 x 24 voxels of gate 0 from the
+    // source voxel down, clipped to the grid
+    int tlo[4] = {0, 0, 0, 0}, tsz[4] = {0, 0, 0, 0};
+    if (accum == kAccCompensated) {
+        const bool automatic = !(cfg->tile_size[0] | cfg->tile_size[1] | cfg->tile_size[2] |
+                                 cfg->tile_size[3]);
+        const int dims[4] = {(int)s->nx, (int)s->ny, (int)s->nz, (int)cfg->n_gates};
+        if (automatic) {
+            const int want[4] = {16, 16, 24, 1};
+            for (int a = 0; a < 4; ++a) {
+                int c = a < 3 ? (int)std::floor(s->src_pos[a] / s->h) : 0;
+                c = std::min(std::max(c, 0), dims[a] - 1);
+                int lo = a < 2 ? c - want[a] / 2 : c;
+                lo = std::min(std::max(lo, 0), std::max(dims[a] - want[a], 0));
+                tlo[a] = lo;
+                tsz[a] = std::min(want[a], dims[a] - lo);
+            }
+        } else {
+            long long e = 1;
+            for (int a = 0; a < 4; ++a) {
+                tlo[a] = cfg->tile_lo[a];
+                tsz[a] = cfg->tile_size[a];
+                if (tsz[a] < 1 || tlo[a] < 0 || tlo[a] + tsz[a] > dims[a])
+                    return fail(s, MCX_E_ARG, "tile outside the grid or empty");
+                e *= tsz[a];
+            }
+            if (e > kTileMaxEntries)
+                return fail(s, MCX_E_ARG, "tile larger than 6144 (gate, voxel) entries");
+        }
+    }
+    const int tile_e = tsz[0] * tsz[1] * tsz[2] * tsz[3];
+    const auto key = std::make_tuple((int)(n_det > 0), (int)prec, block, (int)s->n_media, n_det,
+                                     accum, tile_e);
     LaunchShape shape;
     auto it = s->shape_cache.find(key);
     if (it == s->shape_cache.end()) {
-        MCX_CUDA(s, walk_query_shape(n_det > 0, prec, block, (int)s->n_media, n_det, &shape),
+        MCX_CUDA(s, walk_query_shape(n_det > 0, prec, accum, block, (int)s->n_media, n_det,
+                                     tile_e, &shape),
                  "querying the walk kernel");
         if (shape.blocks_per_sm < 1) return fail(s, MCX_E_ARG, "block_size does not fit on an SM");
         s->shape_cache[key] = shape;
@@ -445,6 +510,12 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     const uint64_t nflu = nvox * cfg->n_gates;
     const int stride = kRecBase + (int)s->n_media - 1;
     MCX_CUDA(s, s->fluence.ensure(nflu * sizeof(float)), "allocating the fluence map");
+    if (accum == kAccCompensated) {
+        MCX_CUDA(s, s->fluence_lo.ensure(nflu * sizeof(float)), "allocating the fluence map");
+        MCX_CUDA(s, s->fluence64.ensure((size_t)std::max(tile_e, 1) * sizeof(double)), "allocating the tile map");
+    } else if (accum == kAccF64) {
+        MCX_CUDA(s, s->fluence64.ensure(nflu * sizeof(double)), "allocating the FP64 fluence map");
+    }
     MCX_CUDA(s, s->block_tally.ensure((size_t)shape.grid * MCX_NTALLY * sizeof(double)), "allocating");
     MCX_CUDA(s, s->block_stats.ensure((size_t)shape.grid * MCX_NSTAT * 8), "allocating");
     MCX_CUDA(s, s->ctrl.ensure(64), "allocating");
@@ -475,6 +546,12 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     unsigned char *tbase = s->tables.as<unsigned char>();
     p.labels = s->labels.as<uint8_t>();
     p.fluence = s->fluence.as<float>();
+    p.fluence_lo = s->fluence_lo.as<float>();
+    p.fluence64 = s->fluence64.as<double>();
+    for (int a = 0; a < 4; ++a) {
+        p.tile_lo[a] = tlo[a];
+        p.tile_size[a] = tsz[a];
+    }
     p.tab_a = tbase + (size_t)oa;
     p.tab_b = tbase + (size_t)ob;
     p.tab_n = tbase + (size_t)on;
@@ -547,13 +624,20 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
 
     // zero the outputs, walk, reduce
     zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu);
+    if (accum == kAccCompensated) {
+        zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence_lo.as<uint32_t>(), (size_t)nflu);
+        zero_words<<<grid_for((size_t)tile_e / 2 + 1), 256, 0, st>>>(s->fluence64.as<uint32_t>(),
+                                                                     (size_t)std::max(tile_e, 1) * 2);
+    } else if (accum == kAccF64) {
+        zero_words<<<grid_for(nflu / 2 + 1), 256, 0, st>>>(s->fluence64.as<uint32_t>(), (size_t)nflu * 2);
+    }
     zero_words<<<1, 32, 0, st>>>(s->ctrl.as<uint32_t>(), 16);
     if (cfg->exit_log > 0)
         zero_words<<<grid_for(cfg->exit_log * 10 / 4 + 1), 256, 0, st>>>(
             s->exits.as<uint32_t>(), (size_t)cfg->exit_log * sizeof(mcx_exit) / 4);
     MCX_CUDA(s, cudaGetLastError(), "launching the zeroing kernel");
     MCX_CUDA(s, cudaEventRecord(s->ev_start, st), "recording an event");
-    MCX_CUDA(s, walk_launch(p, prec, shape, st), "launching the walk kernel");
+    MCX_CUDA(s, walk_launch(p, prec, accum, shape, st), "launching the walk kernel");
     MCX_CUDA(s, cudaEventRecord(s->ev_stop, st), "recording an event");
     double *out_t = s->out.as<double>();
     finalize_kernel<<<1, 256, 0, st>>>(p.block_tally, p.block_stats, shape.grid,
@@ -563,6 +647,10 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     MCX_CUDA(s, cudaEventRecord(s->ev_done, st), "recording an event");
 
     s->cfg = *cfg;
+    for (int a = 0; a < 4; ++a) {
+        s->tile_lo[a] = tlo[a];
+        s->tile_size[a] = tsz[a];
+    }
     s->shape = shape;
     s->rec_stride = stride;
     s->stream = st;
@@ -614,8 +702,11 @@ mcx_status mcx_last_kernel_ms(mcx_sim *s, float *ms)
     return MCX_OK;
 }
 
-mcx_status mcx_read_fluence(mcx_sim *s, float *dst, uint64_t n_elems, int32_t normalized,
-                            int32_t dst_on_device)
+}  // extern "C"
+
+template <typename T>
+static mcx_status read_fluence_t(mcx_sim *s, T *dst, uint64_t n_elems, int32_t normalized,
+                                 int32_t dst_on_device)
 {
     if (!s) return fail(nullptr, MCX_E_ARG, "sim is NULL");
     if (!dst) return fail(s, MCX_E_ARG, "dst is NULL");
@@ -625,7 +716,16 @@ mcx_status mcx_read_fluence(mcx_sim *s, float *dst, uint64_t n_elems, int32_t no
     const uint64_t n = nvox * s->cfg.n_gates;
     if (n_elems != n) return fail(s, MCX_E_ARG, "n_elems must be n_gates*nx*ny*nz = " + std::to_string(n));
     cudaStream_t st = s->stream;
-    const float *src = s->fluence.as<float>();
+    const int mode = s->cfg.accum_mode;
+    // the raw FP32 map can be copied as it is
+    if (mode == kAccPlain && !normalized && sizeof(T) == sizeof(float)) {
+        MCX_CUDA(s, cudaMemcpyAsync(dst, s->fluence.p, n * sizeof(float),
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
+                 "copying the fluence");
+        if (!dst_on_device) MCX_CUDA(s, cudaStreamSynchronize(st), "waiting for the copy");
+        return MCX_OK;
+    }
+    const float *inv_dev = nullptr;
     if (normalized) {
         // inv_norm[label] = 1 / (mua h^3 N dt), 0 where mua = 0 or N = 0
         std::vector<float> inv(kMaxMedia, 0.f);
@@ -638,27 +738,44 @@ mcx_status mcx_read_fluence(mcx_sim *s, float *dst, uint64_t n_elems, int32_t no
         MCX_CUDA(s, s->inv_norm.ensure(kMaxMedia * sizeof(float)), "allocating");
         MCX_CUDA(s, cudaMemcpyAsync(s->inv_norm.p, inv.data(), kMaxMedia * sizeof(float),
                                     cudaMemcpyHostToDevice, st), "uploading normalisation");
-        float *out = dst;
-        if (!dst_on_device) {
-            MCX_CUDA(s, s->staging.ensure(n * sizeof(float)), "allocating the staging buffer");
-            out = s->staging.as<float>();
-        }
-        normalize_kernel<<<grid_for(n), 256, 0, st>>>(src, s->labels.as<uint8_t>(),
-                                                      s->inv_norm.as<float>(), out, (unsigned)nvox,
-                                                      s->cfg.n_gates);
-        MCX_CUDA(s, cudaGetLastError(), "launching the normalisation");
-        src = out;
-        if (dst_on_device) return MCX_OK;
+        MCX_CUDA(s, cudaStreamSynchronize(st), "uploading normalisation");
+        inv_dev = s->inv_norm.as<float>();
     }
-    if (dst_on_device) {
-        MCX_CUDA(s, cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, st),
-                 "copying the fluence");
-        return MCX_OK;
+    T *out = dst;
+    if (!dst_on_device) {
+        MCX_CUDA(s, s->staging.ensure(n * sizeof(T)), "allocating the staging buffer");
+        out = static_cast<T *>(s->staging.p);
     }
-    MCX_CUDA(s, cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost, st),
+    TileBox tb;
+    for (int a = 0; a < 4; ++a) {
+        tb.lo[a] = s->tile_lo[a];
+        tb.size[a] = s->tile_size[a];
+    }
+    resolve_kernel<T><<<grid_for(n), 256, 0, st>>>(mode, s->fluence.as<float>(),
+                                                   s->fluence_lo.as<float>(),
+                                                   s->fluence64.as<double>(), tb, s->nx, s->ny,
+                                                   (unsigned)nvox, s->cfg.n_gates,
+                                                   s->labels.as<uint8_t>(), inv_dev, out);
+    MCX_CUDA(s, cudaGetLastError(), "launching the fluence read-out");
+    if (dst_on_device) return MCX_OK;
+    MCX_CUDA(s, cudaMemcpyAsync(dst, out, n * sizeof(T), cudaMemcpyDeviceToHost, st),
              "copying the fluence");
     MCX_CUDA(s, cudaStreamSynchronize(st), "waiting for the copy");
     return MCX_OK;
+}
+
+extern "C" {
+
+mcx_status mcx_read_fluence(mcx_sim *s, float *dst, uint64_t n_elems, int32_t normalized,
+                            int32_t dst_on_device)
+{
+    return read_fluence_t<float>(s, dst, n_elems, normalized, dst_on_device);
+}
+
+mcx_status mcx_read_fluence64(mcx_sim *s, double *dst, uint64_t n_elems, int32_t normalized,
+                              int32_t dst_on_device)
+{
+    return read_fluence_t<double>(s, dst, n_elems, normalized, dst_on_device);
 }
 
 int32_t mcx_detected_stride(const mcx_sim *s)
@@ -759,7 +876,8 @@ void mcx_destroy(mcx_sim *s)
     if (!s) return;
     DeviceGuard g(s->device);
     if (s->ran) cudaEventSynchronize(s->ev_done);
-    for (DevBuf *b : {&s->labels, &s->fluence, &s->tables, &s->detb, &s->det_buf, &s->exits,
+    for (DevBuf *b : {&s->labels, &s->fluence, &s->fluence_lo, &s->fluence64, &s->tables,
+                      &s->detb, &s->det_buf, &s->exits,
                       &s->block_tally, &s->block_stats, &s->ctrl, &s->out, &s->staging,
                       &s->inv_norm, &s->sort_keys, &s->sort_vals})
         b->release();

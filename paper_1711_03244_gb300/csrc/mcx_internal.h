@@ -38,7 +38,11 @@ struct RunConsts {
 
 struct WalkParams {
     const uint8_t *labels;            // [nz][ny][nx]
-    float *fluence;                   // [n_gates][nvox] absorbed weight
+    float *fluence;                   // [n_gates][nvox] absorbed weight (accum 1: the hi part)
+    float *fluence_lo;                // accum 1: [n_gates][nvox] the lo part
+    double *fluence64;                // accum 2: [n_gates][nvox]; accum 1: the tile's FP64 map
+    int tile_lo[4];                   // accum 1: tile origin (x, y, z, gate)
+    int tile_size[4];                 // accum 1: tile extent; entries = product
     const void *tab_a;                // [n_media] MedA<R>: mus, 1/mus, mua (voxel units), c0/(n h)
     const void *tab_b;                // [n_media] MedB<R>: g, 1-g^2, 1+g^2, 1/(2g)
     const void *tab_n;                // [n_media] R: refractive index
@@ -87,9 +91,13 @@ size_t walk_table_bytes(Precision prec, int n_media);   // bytes of the 4 tables
 void walk_fill_tables(Precision prec, int n_media, const float *props, float h, void *host_buf,
                       const void **tab_a_off, const void **tab_b_off, const void **tab_n_off,
                       const void **tab_tpl_off);        // offsets into the buffer
-cudaError_t walk_query_shape(bool detectors, Precision prec, int block, int n_media, int n_det,
-                             LaunchShape *shape);
-cudaError_t walk_launch(const WalkParams &p, Precision prec, const LaunchShape &shape,
+// accumulation modes (mcx_run_cfg.accum_mode)
+enum { kAccPlain = 0, kAccCompensated = 1, kAccF64 = 2 };
+constexpr int kTileMaxEntries = 6144;  // (gate, voxel) pairs per block tile, 48 KiB
+
+cudaError_t walk_query_shape(bool detectors, Precision prec, int accum, int block, int n_media,
+                             int n_det, int tile_entries, LaunchShape *shape);
+cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const LaunchShape &shape,
                         cudaStream_t stream);
 // api.cu: the error text mcx_last_error(NULL) returns (per host thread)
 void set_global_error(const std::string &msg);

@@ -167,7 +167,8 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
             d.ready = true;
         }
         if (d.shape_block != block) {
-            const cudaError_t e = walk_query_shape(false, Precision::F32, block, kNaMaxMedia, 0, &d.shape);
+            const cudaError_t e = walk_query_shape(false, Precision::F32, kAccPlain, block, kNaMaxMedia, 0,
+                                                     0, &d.shape);
             if (e != cudaSuccess)
                 return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: ") + cudaGetErrorString(e));
             d.shape_block = block;
@@ -251,7 +252,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.max_events = cfg->max_events_per_photon ? cfg->max_events_per_photon : 100000000ull;
     p.reflect = cfg->reflect;
 
-    e = walk_launch(p, Precision::F32, shape, stream);
+    e = walk_launch(p, Precision::F32, kAccPlain, shape, stream);
     if (e != cudaSuccess)
         return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: walk launch: ") + cudaGetErrorString(e));
     na_finalize<<<1, 256, 0, stream>>>(p.block_tally, shape.grid, (double)cfg->n_photons, tally_dev);

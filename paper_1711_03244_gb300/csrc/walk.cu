@@ -193,17 +193,31 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 
 template <typename R>
 struct SmemLayout {
-    size_t a, b, n, tpl, det, total;
-    __host__ __device__ SmemLayout(int n_media, int n_det)
+    size_t a, b, n, tpl, det, tile, total;
+    __host__ __device__ SmemLayout(int n_media, int n_det, int tile_entries)
     {
         a = 128;
         b = align16(a + sizeof(MedA<R>) * n_media);
         n = align16(b + sizeof(MedB<R>) * n_media);
         tpl = align16(n + sizeof(R) * n_media);
         det = align16(tpl + sizeof(R) * n_media);
-        total = align16(det + sizeof(float4) * n_det);
+        tile = align16(det + sizeof(float4) * n_det);        // float hi[E], then float lo[E]
+        total = align16(tile + 2 * sizeof(float) * tile_entries);
     }
 };
+
+// Adds x to the compensated pair (hi, lo): the atomic returns hi's old value a; the
+// hardware stored s = RN(a + x), so the addition's exact rounding error (Knuth's TwoSum)
+// is recovered locally and accumulated into lo.  hi + lo then carries the sum without
+// the per-addition loss of a single FP32 accumulator.
+__device__ __forceinline__ void pair_add(float *hi, float *lo, float x)
+{
+    const float a = atomicAdd(hi, x);
+    const float s = __fadd_rn(a, x);
+    const float bb = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    if (err != 0.f) atomicAdd(lo, err);
+}
 
 template <typename R> __device__ __forceinline__ const RunConsts<R> &consts(const WalkParams &p);
 template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(const WalkParams &p)
@@ -211,12 +225,16 @@ template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(con
 template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(const WalkParams &p)
 { return p.cd; }
 
-template <typename R, bool DET>
+template <typename R, bool DET, int ACC>
 __global__ void __launch_bounds__(256)
 walk_kernel(const WalkParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const SmemLayout<R> L(p.n_media, DET ? p.n_det : 0);
+    const int tile_e = ACC == kAccCompensated
+        ? p.tile_size[0] * p.tile_size[1] * p.tile_size[2] * p.tile_size[3] : 0;
+    const SmemLayout<R> L(p.n_media, DET ? p.n_det : 0, tile_e);
+    float *s_hi = reinterpret_cast<float *>(smem_raw + L.tile);
+    float *s_lo = s_hi + tile_e;
     double *s_tally = reinterpret_cast<double *>(smem_raw);
     unsigned long long *s_stats = reinterpret_cast<unsigned long long *>(smem_raw + 64);
     MedA<R> *s_a = reinterpret_cast<MedA<R> *>(smem_raw + L.a);
@@ -235,6 +253,8 @@ walk_kernel(const WalkParams p)
         for (int i = threadIdx.x; i < p.n_det; i += blockDim.x) s_det[i] = p.det[i];
     if (threadIdx.x < 8) s_tally[threadIdx.x] = 0.0;
     if (threadIdx.x < 8) s_stats[threadIdx.x] = 0ull;
+    if (ACC == kAccCompensated)
+        for (int i = threadIdx.x; i < 2 * tile_e; i += blockDim.x) s_hi[i] = 0.f;
     __syncthreads();
 
     // per-run constants in the walk's precision (read from the parameter bank)
@@ -262,10 +282,26 @@ walk_kernel(const WalkParams p)
     unsigned pool_left = 0;
     const unsigned last_gate = p.n_gates - 1u;
 
-    // a12 (per run): one atomic per (gate, voxel) run of deposits
+    // a6/a12: one accumulation per (gate, voxel) run of deposits
     auto flush = [&]() {
         if (acc != R(0)) {
-            atomicAdd(p.fluence + (unsigned long long)gate * p.nvox + vlin, float(acc));
+            const unsigned long long idx = (unsigned long long)gate * p.nvox + vlin;
+            if (ACC == kAccPlain) {
+                atomicAdd(p.fluence + idx, float(acc));
+            } else if (ACC == kAccF64) {
+                atomicAdd(p.fluence64 + idx, double(acc));
+            } else {
+                const unsigned tx = (unsigned)(ix - p.tile_lo[0]), ty = (unsigned)(iy - p.tile_lo[1]);
+                const unsigned tz = (unsigned)(iz - p.tile_lo[2]), tg = gate - (unsigned)p.tile_lo[3];
+                if (tx < (unsigned)p.tile_size[0] && ty < (unsigned)p.tile_size[1] &&
+                    tz < (unsigned)p.tile_size[2] && tg < (unsigned)p.tile_size[3]) {
+                    const unsigned k = ((tg * p.tile_size[2] + tz) * p.tile_size[1] + ty) *
+                                       p.tile_size[0] + tx;
+                    pair_add(s_hi + k, s_lo + k, float(acc));
+                } else {
+                    pair_add(p.fluence + idx, p.fluence_lo + idx, float(acc));
+                }
+            }
             ++c_flush;
         }
         acc = R(0);
@@ -557,6 +593,13 @@ walk_kernel(const WalkParams p)
     }
 
     __syncthreads();
+    if (ACC == kAccCompensated) {
+        // the block's tile, flushed once in FP64 into the tile's map
+        for (int k = threadIdx.x; k < tile_e; k += blockDim.x) {
+            const double v = (double)s_hi[k] + (double)s_lo[k];
+            if (v != 0.0) atomicAdd(p.fluence64 + k, v);
+        }
+    }
     if (threadIdx.x < MCX_NTALLY)
         p.block_tally[(size_t)blockIdx.x * MCX_NTALLY + threadIdx.x] = s_tally[threadIdx.x];
     if (threadIdx.x < MCX_NSTAT)
@@ -643,22 +686,22 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
     *ot = (const void *)t;
 }
 
-template <typename R, bool DET>
-cudaError_t shape_for(int block, int n_media, int n_det, LaunchShape *shape)
+template <typename R, bool DET, int ACC>
+cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape *shape)
 {
-    const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0).total;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET>,
+    const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0, tile_e).total;
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET>, block,
-                                                           smem)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC>,
+                                                           block, smem)) != cudaSuccess)
         return e;
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC>)) != cudaSuccess) return e;
     shape->block = block;
     shape->blocks_per_sm = per_sm;
     shape->grid = sms * (per_sm > 0 ? per_sm : 1);
@@ -666,12 +709,43 @@ cudaError_t shape_for(int block, int n_media, int n_det, LaunchShape *shape)
     return cudaSuccess;
 }
 
-template <typename R, bool DET>
+template <typename R, bool DET, int ACC>
 cudaError_t launch(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
 {
-    const size_t smem = SmemLayout<R>(p.n_media, DET ? p.n_det : 0).total;
-    walk_kernel<R, DET><<<s.grid, s.block, smem, st>>>(p);
+    const int tile_e = ACC == kAccCompensated
+        ? p.tile_size[0] * p.tile_size[1] * p.tile_size[2] * p.tile_size[3] : 0;
+    const size_t smem = SmemLayout<R>(p.n_media, DET ? p.n_det : 0, tile_e).total;
+    walk_kernel<R, DET, ACC><<<s.grid, s.block, smem, st>>>(p);
     return cudaGetLastError();
+}
+
+template <typename R, int ACC>
+cudaError_t shape_d(bool det, int block, int nm, int nd, int te, LaunchShape *sh)
+{
+    return det ? shape_for<R, true, ACC>(block, nm, nd, te, sh)
+               : shape_for<R, false, ACC>(block, nm, nd, te, sh);
+}
+
+template <typename R, int ACC>
+cudaError_t launch_d(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
+{
+    return p.n_det > 0 ? launch<R, true, ACC>(p, s, st) : launch<R, false, ACC>(p, s, st);
+}
+
+template <typename R>
+cudaError_t shape_a(bool det, int acc, int block, int nm, int nd, int te, LaunchShape *sh)
+{
+    if (acc == kAccCompensated) return shape_d<R, kAccCompensated>(det, block, nm, nd, te, sh);
+    if (acc == kAccF64) return shape_d<R, kAccF64>(det, block, nm, nd, te, sh);
+    return shape_d<R, kAccPlain>(det, block, nm, nd, te, sh);
+}
+
+template <typename R>
+cudaError_t launch_a(const WalkParams &p, int acc, const LaunchShape &s, cudaStream_t st)
+{
+    if (acc == kAccCompensated) return launch_d<R, kAccCompensated>(p, s, st);
+    if (acc == kAccF64) return launch_d<R, kAccF64>(p, s, st);
+    return launch_d<R, kAccPlain>(p, s, st);
 }
 }  // namespace
 
@@ -688,22 +762,19 @@ void walk_fill_tables(Precision prec, int n_media, const float *props, float h, 
     else fill<float>(n_media, props, h, b, oa, ob, on, ot);
 }
 
-cudaError_t walk_query_shape(bool det, Precision prec, int block, int n_media, int n_det,
-                             LaunchShape *shape)
+cudaError_t walk_query_shape(bool det, Precision prec, int accum, int block, int n_media,
+                             int n_det, int tile_entries, LaunchShape *shape)
 {
     if (prec == Precision::F64)
-        return det ? shape_for<double, true>(block, n_media, n_det, shape)
-                   : shape_for<double, false>(block, n_media, n_det, shape);
-    return det ? shape_for<float, true>(block, n_media, n_det, shape)
-               : shape_for<float, false>(block, n_media, n_det, shape);
+        return shape_a<double>(det, accum, block, n_media, n_det, tile_entries, shape);
+    return shape_a<float>(det, accum, block, n_media, n_det, tile_entries, shape);
 }
 
-cudaError_t walk_launch(const WalkParams &p, Precision prec, const LaunchShape &s,
+cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const LaunchShape &s,
                         cudaStream_t st)
 {
-    const bool det = p.n_det > 0;
-    if (prec == Precision::F64) return det ? launch<double, true>(p, s, st) : launch<double, false>(p, s, st);
-    return det ? launch<float, true>(p, s, st) : launch<float, false>(p, s, st);
+    if (prec == Precision::F64) return launch_a<double>(p, accum, s, st);
+    return launch_a<float>(p, accum, s, st);
 }
 
 cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out)

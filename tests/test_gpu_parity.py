@@ -197,17 +197,20 @@ def _assert_voxelwise(gr, ob, min_vox=1000):
     assert chi < 1.25
 
 
+# Replicates: the GPU runs 8 seeds of 1e6 photons; the oracle's 8 batches hold 5e4 photons
+# each (4e5 in total), large enough that the batch means are close to normal (smaller
+# batches give skewed per-voxel means and heavier t tails than the t-distribution).
 def test_voxelwise_3sigma_c1(g, orc):
-    wl = _c1(100_000)
-    gr = _replicates(wl, 100_000, range(1, 9), 1)
-    ob = _oracle_batches(orc, wl, 100_000, 8)
+    wl = _c1(1_000_000)
+    gr = _replicates(wl, 1_000_000, range(1, 9), 1)
+    ob = _oracle_batches(orc, wl, 400_000, 8)
     _assert_voxelwise(gr, ob)
 
 
 def test_voxelwise_3sigma_c2_gates(g, orc):
-    wl = f32(workloads.c2(n_photons=100_000))
-    gr = _replicates(wl, 100_000, range(1, 9), wl.n_gates)
-    ob = _oracle_batches(orc, wl, 100_000, 8)
+    wl = f32(workloads.c2(n_photons=1_000_000))
+    gr = _replicates(wl, 1_000_000, range(1, 9), wl.n_gates)
+    ob = _oracle_batches(orc, wl, 400_000, 8)
     _assert_voxelwise(gr, ob)
 
 

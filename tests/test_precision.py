@@ -1,0 +1,150 @@
+"""Fluence accumulation precision: plain FP32 atomics (accum_mode 0), compensated FP32
+pairs in block tiles with an FP64 tile flush (1), and FP64 atomics (2, diagnostic).
+
+With the same seed the three modes follow identical photon trajectories (the walk does
+not depend on the accumulation), so comparing their maps isolates accumulation error;
+running the walk itself in FP64 (precision 1) makes the trajectories the oracle's, so
+the map against the FP64 oracle isolates it again, voxel by voxel.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_common import F32_RR, balance, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1711_03244_gb300 import build
+    build.build()
+    import paper_1711_03244_gb300 as m
+    m.load()
+    return m
+
+
+def run_modes(g, wl, n, modes=(0, 1, 2), precision=0, seed=None, **kw):
+    out = {}
+    with g.Simulation.from_workload(wl) as sim:
+        for mode in modes:
+            sim.run(n, n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=wl.seed if seed is None else seed,
+                    accum_mode=mode, precision=precision, rr_threshold=F32_RR,
+                    max_detected=1_000_000 if len(wl.detectors) else 0, **kw)
+            out[mode] = (sim.fluence64(), sim.tally(), sim.kernel_ms())
+    return out
+
+
+def rel_errors(test, ref, floor_frac=1e-6):
+    """relative L2 over the map, and max voxel-relative error where the reference holds at
+    least floor_frac of its maximum"""
+    l2 = np.linalg.norm(test - ref) / np.linalg.norm(ref)
+    m = ref > floor_frac * ref.max()
+    mx = np.max(np.abs(test[m] - ref[m]) / ref[m])
+    return float(l2), float(mx)
+
+
+def test_accum_modes_share_trajectories(g):
+    wl = f32(workloads.c1(n_photons=100_000))
+    r = run_modes(g, wl, 100_000)
+    E0, E1, E2 = r[0][0], r[1][0], r[2][0]
+    for mode in (0, 1, 2):
+        assert r[mode][1] == pytest.approx(r[0][1], rel=1e-9)        # same photons, same fates
+    l2_1, mx_1 = rel_errors(E1, E2)
+    l2_0, mx_0 = rel_errors(E0, E2)
+    print(f"c1 1e5: compensated vs FP64 L2 {l2_1:.2e} max {mx_1:.2e}; "
+          f"plain vs FP64 L2 {l2_0:.2e} max {mx_0:.2e}")
+    assert mx_1 < 1e-6 and l2_1 < 1e-7
+    assert mx_0 < 1e-3
+    for E in (E0, E1, E2):
+        assert abs(E.sum() - r[2][1]["absorbed"]) / r[2][1]["absorbed"] < 1e-6
+
+
+def test_compensated_recovers_stagnating_sums(g):
+    """A 4 mm cube: every voxel takes ~1e8 deposit runs, far past the point where an FP32
+    accumulator drops each addition (addend < half an ulp of the sum)."""
+    labels = np.ones((4, 4, 4), dtype=np.uint8)
+    wl = f32(workloads.Workload("cube4", labels, 1.0, np.array([(0, 0, 1, 1.0),
+                                                                (0.05, 10.0, 0.9, 1.37)]),
+                                0, (2.0, 2.0, 0.0), (0.0, 0.0, 1.0), 0.0, np.zeros((0, 4)),
+                                20_000_000, 1, 5.0, 1, 11))
+    r = run_modes(g, wl, wl.n_photons)
+    E0, E1, E2 = r[0][0], r[1][0], r[2][0]
+    l2_1, mx_1 = rel_errors(E1, E2)
+    l2_0, mx_0 = rel_errors(E0, E2)
+    print(f"cube4 2e7: plain vs FP64 L2 {l2_0:.2e} max {mx_0:.2e}; "
+          f"compensated vs FP64 L2 {l2_1:.2e} max {mx_1:.2e}")
+    assert mx_1 < 1e-6
+    assert l2_0 > 100 * max(l2_1, 1e-9)           # plain FP32 is visibly wrong here
+    # the global (outside-tile) compensated path alone: a one-voxel tile
+    with g.Simulation.from_workload(wl) as sim:
+        sim.run(wl.n_photons, dt_ns=wl.dt_ns, seed=wl.seed, accum_mode=1, rr_threshold=F32_RR,
+                tile_lo=(0, 0, 0, 0), tile_size=(1, 1, 1, 1))
+        Eg = sim.fluence64()
+    l2_g, mx_g = rel_errors(Eg, E2)
+    print(f"cube4 2e7: global compensated pairs vs FP64 L2 {l2_g:.2e} max {mx_g:.2e}")
+    assert l2_g < l2_0
+
+
+def test_fp64_walk_fp64_accumulation_matches_oracle_voxelwise(g, orc):
+    """Trajectories in FP64 on both sides and FP64 accumulation: the maps agree voxel by
+    voxel (a deposit segment that starts within rounding of a gate boundary may land in
+    the neighbouring gate; that is the only allowance)."""
+    wl = f32(workloads.c3(n_photons=20_000))
+    r = run_modes(g, wl, 20_000, modes=(2,), precision=1)
+    E = r[2][0]
+    o = orc.run(wl, rr_threshold=F32_RR)
+    ref = o.energy
+    assert abs(E.sum() - ref.sum()) / ref.sum() < 1e-9
+    m = ref > 1e-12
+    rel = np.abs(E[m] - ref[m]) / ref[m]
+    print(f"c3 2e4 fp64: voxels {m.sum()}, rel diff median {np.median(rel):.1e} "
+          f"q99.99 {np.quantile(rel, 0.9999):.1e}")
+    print(f"  fraction within 1e-9: {np.mean(rel < 1e-9):.6f}")
+    assert np.mean(rel < 1e-9) > 0.999
+    assert np.quantile(rel, 0.9999) < 1e-5
+    assert np.abs(E[~m]).max() < 1e-9
+
+
+@pytest.mark.slow
+def test_precision_study_c3(g, orc):
+    """Layered volume with a Gaussian beam (256x256x128, 50 gates): each accumulation mode's
+    error against the FP64 oracle on the same 1e6 photons, with the walk in FP64 (isolates
+    accumulation) and in FP32 (the product path: trajectory differences included)."""
+    n = 1_000_000
+    wl = f32(workloads.c3(n_photons=n))
+    o = orc.run(wl, rr_threshold=F32_RR)
+    ref = o.energy
+    lines = []
+    for prec in (1, 0):
+        r = run_modes(g, wl, n, precision=prec)
+        for mode in (0, 1, 2):
+            l2, mx = rel_errors(r[mode][0], ref, floor_frac=1e-3)
+            lines.append((prec, mode, l2, mx, r[mode][2]))
+    for prec, mode, l2, mx, ms in lines:
+        print(f"c3 1e6 walk={'fp64' if prec else 'fp32'} accum={mode}: vs oracle L2 {l2:.2e} "
+              f"max(>1e-3 peak) {mx:.2e}, walk {ms:.1f} ms")
+    err = {(p, m): (l2, mx) for p, m, l2, mx, _ in lines}
+    assert err[(1, 2)][0] < 1e-9                   # FP64 walk + FP64 sums = the oracle
+    assert err[(1, 1)][0] < 1e-6                   # compensated: accumulation error only
+    assert err[(1, 0)][0] < 1e-3
+    assert err[(1, 1)][0] <= err[(1, 0)][0]
+
+
+@pytest.mark.slow
+def test_precision_at_1e9_photons_c3(g):
+    """The full 1e9-photon layered run (no oracle at this size): plain FP32 and compensated
+    accumulation against the FP64-atomic diagnostic on identical trajectories."""
+    n = 1_000_000_000
+    wl = f32(workloads.c3(n_photons=n))
+    r = run_modes(g, wl, n)
+    E2 = r[2][0]
+    l2_0, mx_0 = rel_errors(r[0][0], E2, floor_frac=1e-3)
+    l2_1, mx_1 = rel_errors(r[1][0], E2, floor_frac=1e-3)
+    print(f"c3 1e9: plain vs FP64 L2 {l2_0:.2e} max {mx_0:.2e} ({r[0][2]:.0f} ms); "
+          f"compensated vs FP64 L2 {l2_1:.2e} max {mx_1:.2e} ({r[1][2]:.0f} ms); "
+          f"FP64 atomics {r[2][2]:.0f} ms")
+    assert l2_1 <= l2_0
+    assert abs(balance(r[1][1]) - n) / n < 1e-5
