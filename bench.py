@@ -338,6 +338,7 @@ def main():
             "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "photons_per_step": n,
                        "photons_per_rank": n, "seed": wl.seed,
                        "l2": "flushed between timed steps (256 MiB write)",
+                       "accumulation": "FP64 L2 atomics per (gate, voxel) run (accum_mode 2)",
                        "launch": info, "parallelism": f"photon-id ranges x{world}"},
             "gpu_launches": 4 * args.steps,
             "wall_s": wall,

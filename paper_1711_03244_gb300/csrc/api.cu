@@ -289,7 +289,7 @@ void mcx_run_cfg_default(mcx_run_cfg *c)
     c->max_detected = 0;
     c->exit_log = 0;
     c->max_events_per_photon = 0;
-    c->accum_mode = 0;
+    c->accum_mode = 2;      // FP64 atomics: exact, and as fast as FP32 atomics on GB300
     c->block_size = 0;
     c->grid_size = 0;
     c->precision = 0;

@@ -155,6 +155,13 @@ __device__ __forceinline__ void rotate(R &ux, R &uy, R &uz, R ct, R st, R sp, R 
         uy = ny;
         uz = nz;
     }
+    // Renormalise: rounding (and the hardware sine/cosine, whose squares do not sum to
+    // exactly 1) would otherwise let |u| drift over thousands of scattering events, and
+    // a photon would then cover more space than the path it is attenuated over.
+    const R inv_n = M<R>::rsqrt(ux * ux + uy * uy + uz * uz);
+    ux *= inv_n;
+    uy *= inv_n;
+    uz *= inv_n;
 }
 
 // Unpolarised Fresnel reflectance n1 -> n2 at incidence cosine ci, given sin^2 of the

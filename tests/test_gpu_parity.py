@@ -197,20 +197,22 @@ def _assert_voxelwise(gr, ob, min_vox=1000):
     assert chi < 1.25
 
 
-# Replicates: the GPU runs 8 seeds of 1e6 photons; the oracle's 8 batches hold 5e4 photons
-# each (4e5 in total), large enough that the batch means are close to normal (smaller
-# batches give skewed per-voxel means and heavier t tails than the t-distribution).
+# Replicates: 8 GPU runs (seeds 1..8) and 8 oracle batches, 1e5 photons each on both
+# sides.  Equal batch sizes keep the Welch statistic symmetric: per-voxel batch means are
+# right-skewed in low-count voxels, and against a near-exact other side (many more
+# photons) a skewed side's low means come with low variances, which inflates positive t
+# beyond the t-distribution even without any bias.
 def test_voxelwise_3sigma_c1(g, orc):
-    wl = _c1(1_000_000)
-    gr = _replicates(wl, 1_000_000, range(1, 9), 1)
-    ob = _oracle_batches(orc, wl, 400_000, 8)
+    wl = _c1(100_000)
+    gr = _replicates(wl, 100_000, range(1, 9), 1)
+    ob = _oracle_batches(orc, wl, 800_000, 8)
     _assert_voxelwise(gr, ob)
 
 
 def test_voxelwise_3sigma_c2_gates(g, orc):
-    wl = f32(workloads.c2(n_photons=1_000_000))
-    gr = _replicates(wl, 1_000_000, range(1, 9), wl.n_gates)
-    ob = _oracle_batches(orc, wl, 400_000, 8)
+    wl = f32(workloads.c2(n_photons=100_000))
+    gr = _replicates(wl, 100_000, range(1, 9), wl.n_gates)
+    ob = _oracle_batches(orc, wl, 800_000, 8)
     _assert_voxelwise(gr, ob)
 
 

@@ -30,13 +30,14 @@ def g():
 
 def _regular(g, wl, n, seed):
     with g.Simulation.from_workload(wl.with_(detectors=np.zeros((0, 4)))) as sim:
-        sim.run(n, n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=seed, rr_threshold=F32_RR)
+        sim.run(n, n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=seed, rr_threshold=F32_RR,
+                accum_mode=0)
         return sim.fluence(), sim.tally()
 
 
 def _noalloc(g, torch, wl, n, seed, labels_dev, flu, tally, stream):
     cfg = g.mcx_run_cfg_default(n_photons=n, n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=seed,
-                                rr_threshold=F32_RR, cuda_stream=stream)
+                                rr_threshold=F32_RR, accum_mode=0, cuda_stream=stream)
     g.mcx_run_noalloc(labels_dev, wl.voxel_mm, wl.media, wl.src_kind, wl.src_pos, wl.src_dir,
                       wl.waist_mm, cfg, flu, tally)
     stream.synchronize()
@@ -76,17 +77,17 @@ def test_noalloc_rejects_sizes_beyond_its_limits(g):
     tally = torch.zeros(6, dtype=torch.float64, device="cuda")
     many = np.tile(wl.media[1], (40, 1))
     many[0] = wl.media[0]
-    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0)
+    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0, accum_mode=0)
     with pytest.raises(g.McxError) as e:
         g.mcx_run_noalloc(labels_dev, 1.0, many, 0, wl.src_pos, wl.src_dir, 0.0, cfg, flu, tally)
     assert e.value.status == g.MCX_E_ARG and "n_media" in str(e.value)
-    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0, grid_size=4096)
+    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0, grid_size=4096, accum_mode=0)
     with pytest.raises(g.McxError) as e:
         g.mcx_run_noalloc(labels_dev, 1.0, wl.media, 0, wl.src_pos, wl.src_dir, 0.0, cfg, flu, tally)
     assert e.value.status == g.MCX_E_ARG and "grid_size" in str(e.value)
     bad = labels_dev.clone()
     bad[0, 0, 0] = 9
-    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0)
+    cfg = g.mcx_run_cfg_default(n_photons=10, dt_ns=5.0, accum_mode=0)
     with pytest.raises(g.McxError) as e:
         g.mcx_run_noalloc(bad, 1.0, wl.media, 0, wl.src_pos, wl.src_dir, 0.0, cfg, flu, tally)
     assert e.value.status == g.MCX_E_STATE
