@@ -183,6 +183,51 @@ def run_reference(args, wl, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def study_paper(args):
+    """The paper's benchmarks (60 mm cube, pencil beam, 1e8 photons; B2/B2a with the
+    r = 15 mm sphere; B1 terminates at the boundary), each step timed like the main bench.
+    Rows: accumulation plain FP32 / FP64 / compensated tiles (this build's counterpart of
+    the paper's non-atomic B2 vs atomic B2a comparison: B2's racy adds are not built), and
+    photon distribution dynamic vs the static per-thread split (the paper's Fig. 3a)."""
+    import torch
+    import paper_1711_03244_gb300 as mcx
+    from paper_1711_03244_gb300 import build as mcx_build
+    mcx_build.build()
+    mcx.load()
+    stream = torch.cuda.current_stream()
+    rows = [("B1", 2, 0), ("B1", 0, 0), ("B1", 1, 0), ("B1", 2, 1),
+            ("B2a", 2, 0), ("B2a", 0, 0), ("B2a", 1, 0), ("B2a", 2, 1)]
+    for name, accum, claim in rows:
+        wl = workloads.paper_b("B1" if name == "B1" else "B2", n_photons=args.photons)
+        with mcx.Simulation.from_workload(wl) as sim:
+            def step():
+                cfg = mcx.mcx_run_cfg_default(n_photons=wl.n_photons, n_gates=wl.n_gates,
+                                              dt_ns=wl.dt_ns, seed=wl.seed, reflect=wl.reflect,
+                                              accum_mode=accum, claim_mode=claim,
+                                              cuda_stream=stream)
+                mcx.mcx_run(sim.handle, cfg)
+            for _ in range(args.warmup):
+                step()
+                mcx.mcx_sync(sim.handle, allow_cap=True)
+            ms = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            stats = mcx.mcx_read_stats(sim.handle)
+        best = min(ms)
+        print(json.dumps({"study": "paper", "workload": name, "photons": wl.n_photons,
+                          "accum_mode": accum, "claim_mode": claim,
+                          "photons_per_ms_best": wl.n_photons / best,
+                          "photons_per_ms_median": wl.n_photons / float(np.median(ms)),
+                          "ms_best": best, "scatter_per_photon": stats["scatter"] / wl.n_photons,
+                          "face_per_photon": stats["face"] / wl.n_photons}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,12 +241,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-model", action="store_true",
                     help="skip the pilot runs of the linear runtime model T = a n + T0")
+    ap.add_argument("--study", default=None, choices=["paper"],
+                    help="paper: the paper's benchmarks B1/B2/B2a under each accumulation and "
+                         "photon-distribution mode (one JSON line each) instead of the bench")
     args = ap.parse_args()
 
     world, rank, local = dist_env()
     wl = workloads.c2(n_photons=args.photons)
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
+        return
+    if args.study == "paper":
+        study_paper(args)
         return
 
     import torch

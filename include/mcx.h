@@ -109,6 +109,13 @@ typedef struct mcx_run_cfg {
     int32_t tile_size[4];          /* and extent; all zero = automatic: 16 x 16 x 24 voxels of
                                       gate 0 from the source voxel down, clipped to the grid;
                                       at most 6144 (gate, voxel) entries (48 KiB per block) */
+    int32_t claim_mode;            /* photon distribution: 0 = dynamic (a warp claims 32 ids
+                                      at a time from a global counter as its lanes finish);
+                                      1 = static per-thread split (thread k of T simulates
+                                      ids k, k+T, k+2T, ...), the paper's thread-level
+                                      baseline in its load-balancing comparison (Fig. 3a);
+                                      FP32 walk only */
+    int32_t reserved1;
 } mcx_run_cfg;
 
 /* Fate and end state of one logged photon (fixed-seed parity log). */

@@ -59,6 +59,8 @@ class McxRunCfg(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("tile_lo", ctypes.c_int32 * 4),
         ("tile_size", ctypes.c_int32 * 4),
+        ("claim_mode", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 

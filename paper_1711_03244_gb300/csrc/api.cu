@@ -453,6 +453,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     const int block = cfg->block_size ? cfg->block_size : 256;
     if (block < 32 || block > 256 || block % 32) return fail(s, MCX_E_ARG, "block_size: 32..256, multiple of 32");
     if (cfg->grid_size < 0) return fail(s, MCX_E_ARG, "grid_size < 0");
+    if (cfg->claim_mode != 0 && cfg->claim_mode != 1) return fail(s, MCX_E_ARG, "claim_mode is 0 or 1");
 
     DeviceGuard guard(s->device);
     if (!guard.ok) return fail(s, MCX_E_CUDA, "cannot select the handle's device");
@@ -491,13 +492,16 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
         }
     }
     const int tile_e = tsz[0] * tsz[1] * tsz[2] * tsz[3];
-    const auto key = std::make_tuple((int)(n_det > 0), (int)prec, block, (int)s->n_media, n_det,
-                                     accum, tile_e);
+    const bool claim_static = cfg->claim_mode == 1;
+    if (claim_static && prec == Precision::F64)
+        return fail(s, MCX_E_ARG, "claim_mode 1 needs precision 0");
+    const auto key = std::make_tuple((int)(n_det > 0) + 2 * (int)claim_static, (int)prec, block,
+                                     (int)s->n_media, n_det, accum, tile_e);
     LaunchShape shape;
     auto it = s->shape_cache.find(key);
     if (it == s->shape_cache.end()) {
         MCX_CUDA(s, walk_query_shape(n_det > 0, prec, accum, block, (int)s->n_media, n_det,
-                                     tile_e, &shape),
+                                     tile_e, claim_static, &shape),
                  "querying the walk kernel");
         if (shape.blocks_per_sm < 1) return fail(s, MCX_E_ARG, "block_size does not fit on an SM");
         s->shape_cache[key] = shape;
@@ -621,6 +625,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.exit_log = cfg->exit_log;
     p.max_events = cfg->max_events_per_photon ? cfg->max_events_per_photon : 100000000ull;
     p.reflect = cfg->reflect;
+    p.claim_static = cfg->claim_mode == 1;
 
     // zero the outputs, walk, reduce
     zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu);

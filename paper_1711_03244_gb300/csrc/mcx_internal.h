@@ -76,6 +76,7 @@ struct WalkParams {
     unsigned long long exit_log;
     unsigned long long max_events;
     int reflect;
+    int claim_static;                 // 1: static per-thread photon split
 };
 
 struct LaunchShape {
@@ -96,7 +97,7 @@ enum { kAccPlain = 0, kAccCompensated = 1, kAccF64 = 2 };
 constexpr int kTileMaxEntries = 6144;  // (gate, voxel) pairs per block tile, 48 KiB
 
 cudaError_t walk_query_shape(bool detectors, Precision prec, int accum, int block, int n_media,
-                             int n_det, int tile_entries, LaunchShape *shape);
+                             int n_det, int tile_entries, bool claim_static, LaunchShape *shape);
 cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const LaunchShape &shape,
                         cudaStream_t stream);
 // api.cu: the error text mcx_last_error(NULL) returns (per host thread)

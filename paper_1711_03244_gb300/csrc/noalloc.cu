@@ -168,7 +168,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
         }
         if (d.shape_block != block) {
             const cudaError_t e = walk_query_shape(false, Precision::F32, kAccPlain, block, kNaMaxMedia, 0,
-                                                     0, &d.shape);
+                                                     0, false, &d.shape);
             if (e != cudaSuccess)
                 return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: ") + cudaGetErrorString(e));
             d.shape_block = block;

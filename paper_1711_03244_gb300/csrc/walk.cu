@@ -155,13 +155,6 @@ __device__ __forceinline__ void rotate(R &ux, R &uy, R &uz, R ct, R st, R sp, R 
         uy = ny;
         uz = nz;
     }
-    // Renormalise: rounding (and the hardware sine/cosine, whose squares do not sum to
-    // exactly 1) would otherwise let |u| drift over thousands of scattering events, and
-    // a photon would then cover more space than the path it is attenuated over.
-    const R inv_n = M<R>::rsqrt(ux * ux + uy * uy + uz * uz);
-    ux *= inv_n;
-    uy *= inv_n;
-    uz *= inv_n;
 }
 
 // Unpolarised Fresnel reflectance n1 -> n2 at incidence cosine ci, given sin^2 of the
@@ -232,8 +225,8 @@ template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(con
 template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(const WalkParams &p)
 { return p.cd; }
 
-template <typename R, bool DET, int ACC>
-__global__ void __launch_bounds__(256)
+template <typename R, bool DET, int ACC, bool STATIC>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
 walk_kernel(const WalkParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -273,7 +266,7 @@ walk_kernel(const WalkParams p)
     const unsigned max_ev = p.max_events < 0xffffffffull ? (unsigned)p.max_events : 0xffffffffu;
 
     bool alive = false, done = false;
-    unsigned long long pid = 0;
+    unsigned long long pid = ~0ull;   // current (or last) photon id; none yet
     Rng rng;
     rng.x = rng.y = 0;
     int ix = 0, iy = 0, iz = 0, lab = 0;
@@ -327,7 +320,12 @@ walk_kernel(const WalkParams p)
                 const unsigned n = __popc(need);
                 const unsigned rank = __popc(need & lt_mask);
                 unsigned long long id;
-                if (pool_left >= n) {
+                if (STATIC) {
+                    // the paper's thread-level split: thread g of T takes g, g + T, g + 2T,
+                    // ...; the next id follows from the lane's previous one
+                    const unsigned long long g0 = blockIdx.x * blockDim.x + threadIdx.x;
+                    id = pid == ~0ull ? g0 : pid - p.photon_offset + gridDim.x * blockDim.x;
+                } else if (pool_left >= n) {
                     id = pool_next + rank;
                     pool_next += n;
                     pool_left -= n;
@@ -693,22 +691,22 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
     *ot = (const void *)t;
 }
 
-template <typename R, bool DET, int ACC>
+template <typename R, bool DET, int ACC, bool ST>
 cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape *shape)
 {
     const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0, tile_e).total;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC>,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC, ST>,
                                                            block, smem)) != cudaSuccess)
         return e;
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC, ST>)) != cudaSuccess) return e;
     shape->block = block;
     shape->blocks_per_sm = per_sm;
     shape->grid = sms * (per_sm > 0 ? per_sm : 1);
@@ -716,35 +714,51 @@ cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape
     return cudaSuccess;
 }
 
-template <typename R, bool DET, int ACC>
+template <typename R, bool DET, int ACC, bool ST>
 cudaError_t launch(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
 {
     const int tile_e = ACC == kAccCompensated
         ? p.tile_size[0] * p.tile_size[1] * p.tile_size[2] * p.tile_size[3] : 0;
     const size_t smem = SmemLayout<R>(p.n_media, DET ? p.n_det : 0, tile_e).total;
-    walk_kernel<R, DET, ACC><<<s.grid, s.block, smem, st>>>(p);
+    walk_kernel<R, DET, ACC, ST><<<s.grid, s.block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename R, int ACC>
-cudaError_t shape_d(bool det, int block, int nm, int nd, int te, LaunchShape *sh)
+// The static per-thread split (a study of the paper's thread-level balancing) is built for
+// the FP32 walk only, so the default dynamic kernel carries none of its code.
+template <typename R, bool DET, int ACC>
+cudaError_t shape_s(bool st, int block, int nm, int nd, int te, LaunchShape *sh)
 {
-    return det ? shape_for<R, true, ACC>(block, nm, nd, te, sh)
-               : shape_for<R, false, ACC>(block, nm, nd, te, sh);
+    if (st && sizeof(R) == 4) return shape_for<R, DET, ACC, true>(block, nm, nd, te, sh);
+    return shape_for<R, DET, ACC, false>(block, nm, nd, te, sh);
+}
+
+template <typename R, bool DET, int ACC>
+cudaError_t launch_s(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
+{
+    if (p.claim_static && sizeof(R) == 4) return launch<R, DET, ACC, true>(p, s, st);
+    return launch<R, DET, ACC, false>(p, s, st);
+}
+
+template <typename R, int ACC>
+cudaError_t shape_d(bool det, bool st, int block, int nm, int nd, int te, LaunchShape *sh)
+{
+    return det ? shape_s<R, true, ACC>(st, block, nm, nd, te, sh)
+               : shape_s<R, false, ACC>(st, block, nm, nd, te, sh);
 }
 
 template <typename R, int ACC>
 cudaError_t launch_d(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
 {
-    return p.n_det > 0 ? launch<R, true, ACC>(p, s, st) : launch<R, false, ACC>(p, s, st);
+    return p.n_det > 0 ? launch_s<R, true, ACC>(p, s, st) : launch_s<R, false, ACC>(p, s, st);
 }
 
 template <typename R>
-cudaError_t shape_a(bool det, int acc, int block, int nm, int nd, int te, LaunchShape *sh)
+cudaError_t shape_a(bool det, bool st, int acc, int block, int nm, int nd, int te, LaunchShape *sh)
 {
-    if (acc == kAccCompensated) return shape_d<R, kAccCompensated>(det, block, nm, nd, te, sh);
-    if (acc == kAccF64) return shape_d<R, kAccF64>(det, block, nm, nd, te, sh);
-    return shape_d<R, kAccPlain>(det, block, nm, nd, te, sh);
+    if (acc == kAccCompensated) return shape_d<R, kAccCompensated>(det, st, block, nm, nd, te, sh);
+    if (acc == kAccF64) return shape_d<R, kAccF64>(det, st, block, nm, nd, te, sh);
+    return shape_d<R, kAccPlain>(det, st, block, nm, nd, te, sh);
 }
 
 template <typename R>
@@ -770,11 +784,11 @@ void walk_fill_tables(Precision prec, int n_media, const float *props, float h, 
 }
 
 cudaError_t walk_query_shape(bool det, Precision prec, int accum, int block, int n_media,
-                             int n_det, int tile_entries, LaunchShape *shape)
+                             int n_det, int tile_entries, bool claim_static, LaunchShape *shape)
 {
     if (prec == Precision::F64)
-        return shape_a<double>(det, accum, block, n_media, n_det, tile_entries, shape);
-    return shape_a<float>(det, accum, block, n_media, n_det, tile_entries, shape);
+        return shape_a<double>(det, false, accum, block, n_media, n_det, tile_entries, shape);
+    return shape_a<float>(det, claim_static, accum, block, n_media, n_det, tile_entries, shape);
 }
 
 cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const LaunchShape &s,

@@ -28,7 +28,8 @@ def f32(wl: workloads.Workload) -> workloads.Workload:
 
 def gpu_run(wl, n_photons=None, seed=None, exit_log=0, precision=0, max_detected=None,
             block_size=0, grid_size=0, photon_offset=0, rr_threshold=F32_RR, rr_m=10.0,
-            n_gates=None, reflect=None, max_events=0, normalized=False):
+            n_gates=None, reflect=None, max_events=0, normalized=False, claim_mode=0,
+            accum_mode=2):
     """Runs the CUDA path through the C ABI; returns a dict of host outputs."""
     import paper_1711_03244_gb300 as g
     n = wl.n_photons if n_photons is None else n_photons
@@ -42,7 +43,8 @@ def gpu_run(wl, n_photons=None, seed=None, exit_log=0, precision=0, max_detected
                      block_size=block_size, grid_size=grid_size, photon_offset=photon_offset,
                      rr_threshold=rr_threshold, rr_m=rr_m,
                      reflect=wl.reflect if reflect is None else reflect,
-                     max_events_per_photon=max_events)
+                     max_events_per_photon=max_events, claim_mode=claim_mode,
+                     accum_mode=accum_mode)
         out = {
             "status": st,
             "energy": sim.fluence(normalized=normalized),

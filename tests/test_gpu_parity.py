@@ -137,7 +137,10 @@ def test_launch_shape_does_not_change_trajectories(g):
     a = gpu_run(wl, exit_log=3000)
     b = gpu_run(wl, exit_log=3000, block_size=64, grid_size=7)
     c = gpu_run(wl, exit_log=3000, block_size=32, grid_size=1)
+    d = gpu_run(wl, exit_log=3000, claim_mode=1)             # static per-thread split
     assert np.array_equal(a["exits"], b["exits"]) and np.array_equal(a["exits"], c["exits"])
+    assert np.array_equal(a["exits"], d["exits"])
+    assert d["stats"]["photons"] == 3000
 
 
 def test_photon_ranges_compose(g):
