@@ -228,6 +228,51 @@ def study_paper(args):
                           "face_per_photon": stats["face"] / wl.n_photons}), flush=True)
 
 
+def study_batched(args):
+    """The batched workload: 256 seeded volumes (side 32..128 mm, 1-3 ellipsoids, random
+    optics, 1e5..1e7 photons each, 5 gates of 1 ns) as one persistent launch recorded in a
+    CUDA graph with the autotuned shape, against one mcx_run per simulation."""
+    import torch
+    import paper_1711_03244_gb300 as mcx
+    from paper_1711_03244_gb300 import build as mcx_build
+    mcx_build.build()
+    mcx.load()
+    stream = torch.cuda.Stream()
+    sims = workloads.c4()
+    total = sum(w.n_photons for w in sims)
+    with mcx.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl)
+        best = b.autotune(fraction=0.05, n_gates=5, dt_ns=1.0, cuda_stream=stream)
+        cfg = dict(n_gates=5, dt_ns=1.0, block_size=best["block_size"],
+                   claim_chunk=best["claim_chunk"], use_graph=1, cuda_stream=stream)
+        for _ in range(args.warmup):
+            b.run(**cfg)
+        ms = []
+        for _ in range(args.steps):
+            b.run(**cfg)
+            ms.append(b.last_ms())
+        stats = b.stats()
+    # the same simulations one at a time (each a complete mcx_run: zero, walk, reduce)
+    seq_ms = 0.0
+    for wl in sims:
+        with mcx.Simulation.from_workload(wl) as sim:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mcx.mcx_run(sim.handle, mcx.mcx_run_cfg_default(
+                n_photons=wl.n_photons, n_gates=5, dt_ns=1.0, seed=wl.seed, cuda_stream=stream))
+            e1.record(stream)
+            e1.synchronize()
+            seq_ms += e0.elapsed_time(e1)
+    print(json.dumps({"study": "batched", "simulations": len(sims), "photons": total,
+                      "autotuned": best, "batch_ms_best": min(ms),
+                      "batch_photons_per_ms": total / min(ms),
+                      "sequential_ms": seq_ms, "sequential_photons_per_ms": total / seq_ms,
+                      "speedup": seq_ms / min(ms), "photons_simulated": stats["photons"]}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,9 +286,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-model", action="store_true",
                     help="skip the pilot runs of the linear runtime model T = a n + T0")
-    ap.add_argument("--study", default=None, choices=["paper"],
+    ap.add_argument("--study", default=None, choices=["paper", "batched"],
                     help="paper: the paper's benchmarks B1/B2/B2a under each accumulation and "
-                         "photon-distribution mode (one JSON line each) instead of the bench")
+                         "photon-distribution mode; batched: the 256-simulation batch in one "
+                         "launch vs one launch per simulation (one JSON line each)")
     args = ap.parse_args()
 
     world, rank, local = dist_env()
@@ -253,6 +299,9 @@ def main():
         return
     if args.study == "paper":
         study_paper(args)
+        return
+    if args.study == "batched":
+        study_batched(args)
         return
 
     import torch

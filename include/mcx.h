@@ -220,6 +220,66 @@ mcx_status mcx_launch_info(mcx_sim *sim, int32_t out[4]);
 const char *mcx_last_error(const mcx_sim *sim);
 void mcx_destroy(mcx_sim *sim);
 
+/* ---- batched simulations --------------------------------------------------------------
+   Many independent simulations of different volumes, optical properties, sources and
+   photon counts run in ONE persistent launch of the walk: photons of all simulations form
+   one queue, so small simulations do not leave the GPU idle (the paper balances photons
+   within a workgroup and across devices, Fig. 3; this extends the idea across problems).
+   Every simulation's photon p uses the stream of (its seed, p): a batched simulation gives
+   the same per-photon trajectories as the same simulation run alone with mcx_run.
+   All simulations share the time gates, the roulette and reflection settings and the
+   accumulation mode; the walk runs with FP32 photon state; no detectors or exit log. */
+typedef struct mcx_batch mcx_batch;
+
+typedef struct mcx_batch_cfg {
+    uint32_t struct_size;          /* sizeof(mcx_batch_cfg) */
+    uint32_t n_gates;              /* shared time gates [g dt, (g+1) dt) */
+    float dt_ns;
+    int32_t reflect;
+    float rr_threshold;
+    float rr_m;
+    int32_t accum_mode;            /* 0 (FP32 atomics) or 2 (FP64 atomics, default) */
+    int32_t block_size;            /* 0 = 256 (multiple of 32, <= 256) */
+    int32_t claim_chunk;           /* photon ids per warp claim: 0 = 32; 32..4096 */
+    int32_t grid_size;             /* 0 = SMs x resident blocks per SM */
+    uint64_t max_events_per_photon;/* 0 = 1e8 */
+    int32_t use_graph;             /* 1: record the run (zeroing, walk, reductions) as a CUDA
+                                      graph on first use and replay it while the batch and the
+                                      settings stay the same */
+    int32_t reserved0;
+    void *cuda_stream;             /* cudaStream_t (NULL = legacy default; with use_graph the
+                                      library then uses a stream of its own) */
+} mcx_batch_cfg;
+
+void mcx_batch_cfg_default(mcx_batch_cfg *cfg);
+mcx_status mcx_batch_create(mcx_batch **out);
+/* Adds one simulation (arguments as in mcx_create_volume, mcx_set_media, mcx_set_source);
+   inputs are copied; out_id receives its index in the batch.  Invalidates earlier runs. */
+mcx_status mcx_batch_add(mcx_batch *b, uint32_t nx, uint32_t ny, uint32_t nz, float voxel_mm,
+                         const uint8_t *labels, int32_t labels_on_device, uint32_t n_media,
+                         const float *props, int32_t src_kind, const float pos_mm[3],
+                         const float dir[3], float waist_mm, uint64_t n_photons, uint64_t seed,
+                         int32_t *out_id);
+/* Enqueues one run of every simulation in the batch; returns without waiting. */
+mcx_status mcx_batch_run(mcx_batch *b, const mcx_batch_cfg *cfg);
+mcx_status mcx_batch_sync(mcx_batch *b);
+/* Device time of the last run: the whole enqueued sequence (ms). */
+mcx_status mcx_batch_last_ms(mcx_batch *b, float *ms);
+/* Fluence of simulation `id` (float [n_gates][nz][ny][nx]; normalized as in
+   mcx_read_fluence), host or device destination; waits for the run. */
+mcx_status mcx_batch_read_fluence(mcx_batch *b, int32_t id, float *dst, uint64_t n_elems,
+                                  int32_t normalized, int32_t dst_on_device);
+mcx_status mcx_batch_read_tally(mcx_batch *b, int32_t id, double out[MCX_NTALLY]);
+/* Event counters of the whole batch (MCX_STAT_*). */
+mcx_status mcx_batch_read_stats(mcx_batch *b, uint64_t out[MCX_NSTAT]);
+/* Times the batch with every simulation's photon count scaled by `fraction` (0 < f <= 1)
+   for block sizes {128, 256} x claim chunks {32, 64, 128, 256}, and writes the fastest
+   into cfg (block_size, claim_chunk); best_ms receives its time.  Runs on cfg's stream. */
+mcx_status mcx_batch_autotune(mcx_batch *b, mcx_batch_cfg *cfg, double fraction, float *best_ms);
+int32_t mcx_batch_size(const mcx_batch *b);
+const char *mcx_batch_last_error(const mcx_batch *b);
+void mcx_batch_destroy(mcx_batch *b);
+
 /* ---- allocation-free run --------------------------------------------------------------
    The paper has no counterpart to this entry point; it exists for callers that cannot let
    a library allocate device memory: applications whose own pool or caching allocator owns

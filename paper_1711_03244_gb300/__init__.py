@@ -74,6 +74,25 @@ EXIT_DTYPE = np.dtype([("fate", np.int32), ("nscat", np.uint32), ("pos", np.floa
                        ("dir", np.float32, 3), ("w", np.float32), ("t", np.float32)])
 assert EXIT_DTYPE.itemsize == ctypes.sizeof(McxExit) == 40
 
+class McxBatchCfg(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("n_gates", ctypes.c_uint32),
+        ("dt_ns", ctypes.c_float),
+        ("reflect", ctypes.c_int32),
+        ("rr_threshold", ctypes.c_float),
+        ("rr_m", ctypes.c_float),
+        ("accum_mode", ctypes.c_int32),
+        ("block_size", ctypes.c_int32),
+        ("claim_chunk", ctypes.c_int32),
+        ("grid_size", ctypes.c_int32),
+        ("max_events_per_photon", ctypes.c_uint64),
+        ("use_graph", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
 # exported symbols and their signatures (restype, argtypes)
 _P = ctypes.c_void_p
 _u32, _u64, _i32, _f32, _f64 = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
@@ -103,6 +122,20 @@ SIGNATURES = {
     "mcx_destroy": (None, [_P]),
     "mcx_run_noalloc": (_i32, [_P, _u32, _u32, _u32, _f32, _u32, _P, _i32, _P, _P, _f32,
                                ctypes.POINTER(McxRunCfg), _P, _P]),
+    "mcx_batch_cfg_default": (None, [ctypes.POINTER(McxBatchCfg)]),
+    "mcx_batch_create": (_i32, [ctypes.POINTER(_P)]),
+    "mcx_batch_add": (_i32, [_P, _u32, _u32, _u32, _f32, _P, _i32, _u32, _P, _i32, _P, _P, _f32,
+                             _u64, _u64, ctypes.POINTER(_i32)]),
+    "mcx_batch_run": (_i32, [_P, ctypes.POINTER(McxBatchCfg)]),
+    "mcx_batch_sync": (_i32, [_P]),
+    "mcx_batch_last_ms": (_i32, [_P, ctypes.POINTER(_f32)]),
+    "mcx_batch_read_fluence": (_i32, [_P, _i32, _P, _u64, _i32, _i32]),
+    "mcx_batch_read_tally": (_i32, [_P, _i32, _P]),
+    "mcx_batch_read_stats": (_i32, [_P, _P]),
+    "mcx_batch_autotune": (_i32, [_P, ctypes.POINTER(McxBatchCfg), _f64, ctypes.POINTER(_f32)]),
+    "mcx_batch_size": (_i32, [_P]),
+    "mcx_batch_last_error": (ctypes.c_char_p, [_P]),
+    "mcx_batch_destroy": (None, [_P]),
     "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
     "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
 }
@@ -349,6 +382,114 @@ def photon_range(rank: int, world: int, n_per_rank: int) -> Tuple[int, int]:
     if not (0 <= rank < world) or n_per_rank < 0:
         raise ValueError("need 0 <= rank < world and n_per_rank >= 0")
     return rank * n_per_rank, n_per_rank
+
+
+# ------------------------------------------------------------------------ batches
+def _bcheck(b, st: int):
+    if st != MCX_OK:
+        L = load()
+        msg = L.mcx_batch_last_error(b) if b else L.mcx_last_error(None)
+        raise McxError(st, (msg or b"").decode() or L.mcx_status_string(st).decode())
+    return st
+
+
+def mcx_batch_cfg_default(**overrides) -> McxBatchCfg:
+    cfg = McxBatchCfg()
+    load().mcx_batch_cfg_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "cuda_stream":
+            v = _stream_handle(v)
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Batch:
+    """Many simulations in one persistent launch (mcx_batch_* in include/mcx.h)."""
+
+    def __init__(self):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(None, L.mcx_batch_create(ctypes.byref(h)))
+        self.handle = h
+        self.shapes = []
+        self.n_gates = 1
+
+    def add(self, labels, voxel_mm, media, src_kind=0, src_pos=(0, 0, 0), src_dir=(0, 0, 1),
+            waist_mm=0.0, n_photons=0, seed=1) -> int:
+        lab = np.ascontiguousarray(labels, dtype=np.uint8)
+        nz, ny, nx = lab.shape
+        a = np.ascontiguousarray(media, dtype=np.float32).reshape(-1, 4)
+        p = np.ascontiguousarray(src_pos, dtype=np.float32)
+        d = np.ascontiguousarray(src_dir, dtype=np.float32)
+        out = ctypes.c_int32()
+        _bcheck(self.handle, load().mcx_batch_add(self.handle, nx, ny, nz, float(voxel_mm),
+                                                  _ptr(lab), 0, a.shape[0], _ptr(a), int(src_kind),
+                                                  _ptr(p), _ptr(d), float(waist_mm), int(n_photons),
+                                                  int(seed), ctypes.byref(out)))
+        self.shapes.append(lab.shape)
+        return out.value
+
+    def add_workload(self, wl, n_photons=None, seed=None) -> int:
+        return self.add(wl.labels, wl.voxel_mm, wl.media, wl.src_kind, wl.src_pos, wl.src_dir,
+                        wl.waist_mm, wl.n_photons if n_photons is None else n_photons,
+                        wl.seed if seed is None else seed)
+
+    def run(self, wait=True, **cfg):
+        c = mcx_batch_cfg_default(**cfg)
+        self.n_gates = c.n_gates
+        _bcheck(self.handle, load().mcx_batch_run(self.handle, ctypes.byref(c)))
+        if wait:
+            _bcheck(self.handle, load().mcx_batch_sync(self.handle))
+
+    def last_ms(self) -> float:
+        ms = ctypes.c_float()
+        _bcheck(self.handle, load().mcx_batch_last_ms(self.handle, ctypes.byref(ms)))
+        return ms.value
+
+    def fluence(self, sim_id: int, normalized=False, out=None):
+        if out is None:
+            out = np.zeros((self.n_gates,) + self.shapes[sim_id], dtype=np.float32)
+        n = out.numel() if hasattr(out, "numel") else out.size
+        _bcheck(self.handle, load().mcx_batch_read_fluence(self.handle, sim_id, _ptr(out), n,
+                                                           int(normalized), _on_device(out)))
+        return out
+
+    def tally(self, sim_id: int) -> dict:
+        out = np.zeros(6, dtype=np.float64)
+        _bcheck(self.handle, load().mcx_batch_read_tally(self.handle, sim_id, _ptr(out)))
+        return dict(zip(TALLY_NAMES, out.tolist()))
+
+    def stats(self) -> dict:
+        out = np.zeros(8, dtype=np.uint64)
+        _bcheck(self.handle, load().mcx_batch_read_stats(self.handle, _ptr(out)))
+        return dict(zip(STAT_NAMES, [int(v) for v in out]))
+
+    def autotune(self, fraction=0.05, **cfg):
+        c = mcx_batch_cfg_default(**cfg)
+        ms = ctypes.c_float()
+        _bcheck(self.handle, load().mcx_batch_autotune(self.handle, ctypes.byref(c), float(fraction),
+                                                       ctypes.byref(ms)))
+        return {"block_size": c.block_size, "claim_chunk": c.claim_chunk, "ms": ms.value}
+
+    def __len__(self):
+        return int(load().mcx_batch_size(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().mcx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ------------------------------------------------------------------------ convenience

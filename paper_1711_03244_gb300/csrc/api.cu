@@ -585,19 +585,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
             d.src_pos[a] = s->src_pos[a] / s->h;
             d.src_dir[a] = s->src_dir[a];
         }
-        // Gaussian launch plane: e1 = normalise(dir x z) (x when the beam is along z),
-        // e2 = dir x e1
-        const double *dd = s->src_dir;
-        double e1[3];
-        if (std::fabs(dd[2]) > 0.999999) { e1[0] = 1; e1[1] = 0; e1[2] = 0; }
-        else {
-            const double n1 = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1]);
-            e1[0] = dd[1] / n1; e1[1] = -dd[0] / n1; e1[2] = 0;
-        }
-        for (int a = 0; a < 3; ++a) d.src_e1[a] = e1[a];
-        d.src_e2[0] = dd[1] * e1[2] - dd[2] * e1[1];
-        d.src_e2[1] = dd[2] * e1[0] - dd[0] * e1[2];
-        d.src_e2[2] = dd[0] * e1[1] - dd[1] * e1[0];
+        launch_plane(s->src_dir, d.src_e1, d.src_e2);
         d.waist = s->src_waist / s->h;
         d.rr_threshold = cfg->rr_threshold;
         d.rr_m = cfg->rr_m;
@@ -626,6 +614,7 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.max_events = cfg->max_events_per_photon ? cfg->max_events_per_photon : 100000000ull;
     p.reflect = cfg->reflect;
     p.claim_static = cfg->claim_mode == 1;
+    p.claim_chunk = kClaimChunk;
 
     // zero the outputs, walk, reduce
     zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu);

@@ -14,7 +14,7 @@ constexpr int kMaxMedia = 256;       // label values 0..255
 constexpr int kMaxDetMedia = 33;     // media rows allowed when detectors are present
 constexpr int kMaxDet = 64;
 constexpr int kRecBase = 12;         // detected-record words before the partial paths
-constexpr int kClaimChunk = 32;      // photon ids a warp claims per global atomic
+constexpr int kClaimChunk = 32;      // default photon ids a warp claims per global atomic
 constexpr float kC0 = 299.792458f;   // mm/ns
 
 // device status word bits
@@ -34,6 +34,22 @@ struct RunConsts {
     R rr_threshold;
     R rr_m;
     R rr_inv_m;
+};
+
+// One simulation of a batch (all lengths in its own voxel units).
+struct BatchSim {
+    const uint8_t *labels;            // [nz][ny][nx]
+    float *fluence;                   // accum 0: [n_gates][nvox]
+    double *fluence64;                // accum 2: [n_gates][nvox]
+    double *tally;                    // [MCX_NTALLY], FP64 atomics
+    unsigned long long first;         // first flattened photon index of this simulation
+    unsigned long long n_photons;
+    unsigned long long seed;
+    int nx, ny, nz;
+    unsigned nvox;
+    int tab0;                         // first row of this simulation in the batch tables
+    int src_kind;
+    float src_pos[3], src_dir[3], src_e1[3], src_e2[3], waist;
 };
 
 struct WalkParams {
@@ -77,6 +93,9 @@ struct WalkParams {
     unsigned long long max_events;
     int reflect;
     int claim_static;                 // 1: static per-thread photon split
+    unsigned claim_chunk;             // photon ids a warp claims per global atomic (>= 32)
+    const BatchSim *sims;             // batch: [n_sims], ordered by `first`
+    int n_sims;
 };
 
 struct LaunchShape {
@@ -100,6 +119,26 @@ cudaError_t walk_query_shape(bool detectors, Precision prec, int accum, int bloc
                              int n_det, int tile_entries, bool claim_static, LaunchShape *shape);
 cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const LaunchShape &shape,
                         cudaStream_t stream);
+// batch walk: FP32 photon state, accumulation 0 or 2, no detectors or exit log
+cudaError_t walk_batch_query_shape(int accum, int block, LaunchShape *shape);
+cudaError_t walk_batch_launch(const WalkParams &p, int accum, const LaunchShape &shape,
+                              cudaStream_t stream);
+// Gaussian launch plane of a beam along unit vector d: e1 = normalise(d x z) (x when the
+// beam is along z), e2 = d x e1.
+inline void launch_plane(const double d[3], double e1[3], double e2[3])
+{
+    if (d[2] > 0.999999 || d[2] < -0.999999) {
+        e1[0] = 1; e1[1] = 0; e1[2] = 0;
+    } else {
+        double n1 = d[0] * d[0] + d[1] * d[1];
+        n1 = n1 > 0 ? 1.0 / __builtin_sqrt(n1) : 0.0;
+        e1[0] = d[1] * n1; e1[1] = -d[0] * n1; e1[2] = 0;
+    }
+    e2[0] = d[1] * e1[2] - d[2] * e1[1];
+    e2[1] = d[2] * e1[0] - d[0] * e1[2];
+    e2[2] = d[0] * e1[1] - d[1] * e1[0];
+}
+
 // api.cu: the error text mcx_last_error(NULL) returns (per host thread)
 void set_global_error(const std::string &msg);
 

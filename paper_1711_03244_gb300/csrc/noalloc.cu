@@ -227,14 +227,9 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     c.dt = cfg->dt_ns;
     c.inv_dt = (float)(1.0 / (double)cfg->dt_ns);
     c.t_end = (float)((double)cfg->dt_ns * cfg->n_gates);
-    double d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn}, e1[3];
-    if (std::fabs(d[2]) > 0.999999) { e1[0] = 1; e1[1] = 0; e1[2] = 0; }
-    else {
-        const double n1 = std::sqrt(d[0] * d[0] + d[1] * d[1]);
-        e1[0] = d[1] / n1; e1[1] = -d[0] / n1; e1[2] = 0;
-    }
-    const double e2[3] = {d[1] * e1[2] - d[2] * e1[1], d[2] * e1[0] - d[0] * e1[2],
-                          d[0] * e1[1] - d[1] * e1[0]};
+    const double d[3] = {dir[0] / dn, dir[1] / dn, dir[2] / dn};
+    double e1[3], e2[3];
+    launch_plane(d, e1, e2);
     for (int a = 0; a < 3; ++a) {
         c.src_pos[a] = (float)((double)pos_mm[a] / voxel_mm);
         c.src_dir[a] = (float)d[a];
@@ -251,6 +246,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.seed = cfg->seed;
     p.max_events = cfg->max_events_per_photon ? cfg->max_events_per_photon : 100000000ull;
     p.reflect = cfg->reflect;
+    p.claim_chunk = kClaimChunk;
 
     e = walk_launch(p, Precision::F32, kAccPlain, shape, stream);
     if (e != cudaSuccess)

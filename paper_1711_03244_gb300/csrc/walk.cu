@@ -225,8 +225,8 @@ template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(con
 template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(const WalkParams &p)
 { return p.cd; }
 
-template <typename R, bool DET, int ACC, bool STATIC>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
+template <typename R, bool DET, int ACC, bool STATIC, bool BATCH>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BATCH ? 3 : 4) : 1)
 walk_kernel(const WalkParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,7 +243,7 @@ walk_kernel(const WalkParams p)
     R *s_tpl = reinterpret_cast<R *>(smem_raw + L.tpl);
     float4 *s_det = reinterpret_cast<float4 *>(smem_raw + L.det);
 
-    for (int i = threadIdx.x; i < p.n_media; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (BATCH ? 0 : p.n_media); i += blockDim.x) {
         s_a[i] = static_cast<const MedA<R> *>(p.tab_a)[i];
         s_b[i] = static_cast<const MedB<R> *>(p.tab_b)[i];
         s_n[i] = static_cast<const R *>(p.tab_n)[i];
@@ -262,7 +262,41 @@ walk_kernel(const WalkParams p)
 
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
+
+    // Geometry of the photon's simulation: the kernel parameters, or (batch) the lane's
+    // current simulation, loaded at each launch.
+    const uint8_t *G_labels = p.labels;
+    float *G_flu = p.fluence;
+    double *G_flu64 = p.fluence64;
+    int G_nx = p.nx, G_ny = p.ny, G_nz = p.nz;
+    unsigned G_nvox = p.nvox;
+    int tab0 = 0, sim = 0;
+    unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
+    // per-label tables: shared memory, or (batch) the batch tables through L1
+    auto medA = [&](int l) -> MedA<R> {
+        if constexpr (BATCH) {
+            const float4 v = __ldg(static_cast<const float4 *>(p.tab_a) + tab0 + l);
+            return MedA<R>{v.x, v.y, v.z, v.w};
+        } else {
+            return s_a[l];
+        }
+    };
+    auto medB = [&](int l) -> MedB<R> {
+        if constexpr (BATCH) {
+            const float4 v = __ldg(static_cast<const float4 *>(p.tab_b) + tab0 + l);
+            return MedB<R>{v.x, v.y, v.z, v.w};
+        } else {
+            return s_b[l];
+        }
+    };
+    auto med_n = [&](int l) -> R {
+        if constexpr (BATCH) return __ldg(static_cast<const float *>(p.tab_n) + tab0 + l);
+        else return s_n[l];
+    };
+    auto med_tpl = [&](int l) -> R {
+        if constexpr (BATCH) return __ldg(static_cast<const float *>(p.tab_tpl) + tab0 + l);
+        else return s_tpl[l];
+    };
     const unsigned max_ev = p.max_events < 0xffffffffull ? (unsigned)p.max_events : 0xffffffffu;
 
     bool alive = false, done = false;
@@ -285,11 +319,11 @@ walk_kernel(const WalkParams p)
     // a6/a12: one accumulation per (gate, voxel) run of deposits
     auto flush = [&]() {
         if (acc != R(0)) {
-            const unsigned long long idx = (unsigned long long)gate * p.nvox + vlin;
+            const unsigned long long idx = (unsigned long long)gate * G_nvox + vlin;
             if (ACC == kAccPlain) {
-                atomicAdd(p.fluence + idx, float(acc));
+                atomicAdd(G_flu + idx, float(acc));
             } else if (ACC == kAccF64) {
-                atomicAdd(p.fluence64 + idx, double(acc));
+                atomicAdd(G_flu64 + idx, double(acc));
             } else {
                 const unsigned tx = (unsigned)(ix - p.tile_lo[0]), ty = (unsigned)(iy - p.tile_lo[1]);
                 const unsigned tz = (unsigned)(iz - p.tile_lo[2]), tg = gate - (unsigned)p.tile_lo[3];
@@ -331,31 +365,58 @@ walk_kernel(const WalkParams p)
                     pool_left -= n;
                 } else {
                     unsigned long long nb = 0;
-                    if (lane == 0) nb = atomicAdd(p.photon_counter, (unsigned long long)kClaimChunk);
+                    if (lane == 0) nb = atomicAdd(p.photon_counter, (unsigned long long)p.claim_chunk);
                     nb = __shfl_sync(kFull, nb, 0);
                     id = rank < pool_left ? pool_next + rank : nb + (rank - pool_left);
                     const unsigned used_new = n - pool_left;
                     pool_next = nb + used_new;
-                    pool_left = kClaimChunk - used_new;
+                    pool_left = p.claim_chunk - used_new;
                 }
                 if ((need >> lane) & 1u) {
                     if (id >= p.n_photons) {
                         done = true;
                     } else {
                         // ---- a2/a3: per-photon RNG and launch
-                        pid = p.photon_offset + id;
-                        rng.seed(p.seed, pid);
-                        R px = C.src_pos[0], py = C.src_pos[1], pz = C.src_pos[2];
-                        ux = C.src_dir[0]; uy = C.src_dir[1]; uz = C.src_dir[2];
-                        if (p.src_kind == 1) {
+                        R px, py, pz, e1[3], e2[3], waist;
+                        int kind;
+                        if constexpr (BATCH) {
+                            // the simulation holding flattened index id: the last with first <= id
+                            int lo = 0, hi = p.n_sims - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (p.sims[mid].first <= id) lo = mid; else hi = mid - 1;
+                            }
+                            sim = lo;
+                            const BatchSim &S = p.sims[sim];
+                            pid = id - S.first;
+                            rng.seed(S.seed, pid);
+                            G_labels = S.labels; G_flu = S.fluence; G_flu64 = S.fluence64;
+                            G_nx = S.nx; G_ny = S.ny; G_nz = S.nz; G_nvox = S.nvox;
+                            nxy = (unsigned)S.nx * (unsigned)S.ny;
+                            tab0 = S.tab0;
+                            px = S.src_pos[0]; py = S.src_pos[1]; pz = S.src_pos[2];
+                            ux = S.src_dir[0]; uy = S.src_dir[1]; uz = S.src_dir[2];
+                            for (int a = 0; a < 3; ++a) { e1[a] = S.src_e1[a]; e2[a] = S.src_e2[a]; }
+                            waist = S.waist;
+                            kind = S.src_kind;
+                        } else {
+                            pid = p.photon_offset + id;
+                            rng.seed(p.seed, pid);
+                            px = C.src_pos[0]; py = C.src_pos[1]; pz = C.src_pos[2];
+                            ux = C.src_dir[0]; uy = C.src_dir[1]; uz = C.src_dir[2];
+                            for (int a = 0; a < 3; ++a) { e1[a] = C.src_e1[a]; e2[a] = C.src_e2[a]; }
+                            waist = C.waist;
+                            kind = p.src_kind;
+                        }
+                        if (kind == 1) {
                             float f1, f2;
                             rng.pair(f1, f2);
-                            const R r = C.waist * M<R>::sqrt(-M<R>::log(R(f1)) * R(0.5));
+                            const R r = waist * M<R>::sqrt(-M<R>::log(R(f1)) * R(0.5));
                             R sn, cs;
                             M<R>::sincos_2pi(R(f2), &sn, &cs);
-                            px += r * (cs * C.src_e1[0] + sn * C.src_e2[0]);
-                            py += r * (cs * C.src_e1[1] + sn * C.src_e2[1]);
-                            pz += r * (cs * C.src_e1[2] + sn * C.src_e2[2]);
+                            px += r * (cs * e1[0] + sn * e2[0]);
+                            py += r * (cs * e1[1] + sn * e2[1]);
+                            pz += r * (cs * e1[2] + sn * e2[2]);
                         }
                         const R fx = floor(px), fy = floor(py), fz = floor(pz);
                         ix = (int)fx - ((px == fx && ux < R(0)) ? 1 : 0);
@@ -369,17 +430,18 @@ walk_kernel(const WalkParams p)
                         nscat = nrr = c_face = c_fres = c_flush = c_rr = 0;
                         if (DET)
                             for (int m = 0; m < p.n_media && m < kMaxDetMedia; ++m) Lpath[m] = 0.f;
-                        const bool inside = (unsigned)ix < (unsigned)p.nx &&
-                                            (unsigned)iy < (unsigned)p.ny &&
-                                            (unsigned)iz < (unsigned)p.nz;
-                        vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)p.nx + (unsigned)ix) : 0u;
-                        lab = inside ? (int)__ldg(p.labels + vlin) : 0;
+                        const bool inside = (unsigned)ix < (unsigned)G_nx &&
+                                            (unsigned)iy < (unsigned)G_ny &&
+                                            (unsigned)iz < (unsigned)G_nz;
+                        vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)G_nx + (unsigned)ix) : 0u;
+                        lab = inside ? (int)__ldg(G_labels + vlin) : 0;
                         alive = lab != 0;
                         if (alive) {
                             new_hop();
                         } else {
                             // launched outside the medium: counted as escaped, never enters
-                            atomicAdd(&s_tally[MCX_TALLY_ESCAPED], 1.0);
+                            if constexpr (BATCH) atomicAdd(p.sims[sim].tally + MCX_TALLY_ESCAPED, 1.0);
+                            else atomicAdd(&s_tally[MCX_TALLY_ESCAPED], 1.0);
                             atomicAdd(&s_stats[MCX_STAT_PHOTONS], 1ull);
                             const unsigned long long rel = pid - p.photon_offset;
                             if (rel < p.exit_log) {
@@ -411,7 +473,7 @@ walk_kernel(const WalkParams p)
                 gate = g2 < last_gate ? g2 : last_gate;
                 t_next = gate < last_gate ? R(gate + 1u) * C.dt : M<R>::huge();
             }
-            const MedA<R> A = s_a[lab];
+            const MedA<R> A = medA(lab);
             // ---- a5: nearest face (lowest axis on ties), scattering point, time limit
             // (a fraction that rounding pushed past its face gives a zero-length step)
             const R dxf = face_dist(qx, iux);
@@ -432,7 +494,7 @@ walk_kernel(const WalkParams p)
             qx += l * ux;
             qy += l * uy;
             qz += l * uz;
-            t += l * s_tpl[lab];
+            t += l * med_tpl(lab);
             s = ev == EV_SCAT ? R(0) : s - l * A.mus;
             if (DET) Lcur += l;
             const R wn = w * M<R>::exp(-A.mua * l);
@@ -450,11 +512,11 @@ walk_kernel(const WalkParams p)
                 const bool up = ua >= R(0);
                 const R qb = up ? R(1) : R(0);
                 const int ia = (ax == 0 ? ix : (ax == 1 ? iy : iz)) + (up ? 1 : -1);
-                const int dim = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
-                const unsigned stride = ax == 0 ? 1u : (ax == 1 ? (unsigned)p.nx : nxy);
+                const int dim = ax == 0 ? G_nx : (ax == 1 ? G_ny : G_nz);
+                const unsigned stride = ax == 0 ? 1u : (ax == 1 ? (unsigned)G_nx : nxy);
                 const unsigned nlin = up ? vlin + stride : vlin - stride;
                 const bool inside = (unsigned)ia < (unsigned)dim;
-                const int b = inside ? (int)__ldg(p.labels + nlin) : 0;
+                const int b = inside ? (int)__ldg(G_labels + nlin) : 0;
                 // photon on the face
                 qx = ax == 0 ? qb : qx;
                 qy = ax == 1 ? qb : qy;
@@ -466,7 +528,7 @@ walk_kernel(const WalkParams p)
                     // the paper's B1: the exterior terminates, internal mismatches pass
                     if (b == 0) escape = true; else enter = true;
                 } else {
-                    const R na = s_n[lab], nb = s_n[b];
+                    const R na = med_n(lab), nb = med_n(b);
                     if (na == nb) {
                         if (b == 0) escape = true; else enter = true;
                     } else {
@@ -515,7 +577,7 @@ walk_kernel(const WalkParams p)
             } else {
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
-                const MedB<R> B = s_b[lab];
+                const MedB<R> B = medB(lab);
                 float xi_hg, xi_phi;
                 rng.pair(xi_hg, xi_phi);
                 R ct, st;
@@ -527,7 +589,10 @@ walk_kernel(const WalkParams p)
                 if (w < C.rr_threshold) {
                     ++c_rr;
                     if (R(rng.uniform()) < C.rr_inv_m) {
-                        atomicAdd(&s_tally[MCX_TALLY_RR_GAINED], double((C.rr_m - R(1)) * w));
+                        if constexpr (BATCH)
+                            atomicAdd(p.sims[sim].tally + MCX_TALLY_RR_GAINED, double((C.rr_m - R(1)) * w));
+                        else
+                            atomicAdd(&s_tally[MCX_TALLY_RR_GAINED], double((C.rr_m - R(1)) * w));
                         w *= C.rr_m;
                         ++nrr;
                     } else {
@@ -543,8 +608,13 @@ walk_kernel(const WalkParams p)
         flush();
         const int slot = fate == MCX_FATE_ESCAPED ? MCX_TALLY_ESCAPED
                        : (fate == MCX_FATE_ROULETTE ? MCX_TALLY_RR_KILLED : MCX_TALLY_TIME);
-        atomicAdd(&s_tally[slot], double(w));
-        atomicAdd(&s_tally[MCX_TALLY_ABSORBED], double(absorbed));
+        if constexpr (BATCH) {
+            atomicAdd(p.sims[sim].tally + slot, double(w));
+            atomicAdd(p.sims[sim].tally + MCX_TALLY_ABSORBED, double(absorbed));
+        } else {
+            atomicAdd(&s_tally[slot], double(w));
+            atomicAdd(&s_tally[MCX_TALLY_ABSORBED], double(absorbed));
+        }
         atomicAdd(&s_stats[MCX_STAT_SCATTER], (unsigned long long)nscat);
         atomicAdd(&s_stats[MCX_STAT_FACE], (unsigned long long)c_face);
         atomicAdd(&s_stats[MCX_STAT_FRESNEL], (unsigned long long)c_fres);
@@ -691,22 +761,22 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
     *ot = (const void *)t;
 }
 
-template <typename R, bool DET, int ACC, bool ST>
+template <typename R, bool DET, int ACC, bool ST, bool BATCH = false>
 cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape *shape)
 {
     const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0, tile_e).total;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC, ST>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC, ST, BATCH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC, ST>,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC, ST, BATCH>,
                                                            block, smem)) != cudaSuccess)
         return e;
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC, ST>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC, ST, BATCH>)) != cudaSuccess) return e;
     shape->block = block;
     shape->blocks_per_sm = per_sm;
     shape->grid = sms * (per_sm > 0 ? per_sm : 1);
@@ -714,13 +784,13 @@ cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape
     return cudaSuccess;
 }
 
-template <typename R, bool DET, int ACC, bool ST>
+template <typename R, bool DET, int ACC, bool ST, bool BATCH = false>
 cudaError_t launch(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
 {
     const int tile_e = ACC == kAccCompensated
         ? p.tile_size[0] * p.tile_size[1] * p.tile_size[2] * p.tile_size[3] : 0;
-    const size_t smem = SmemLayout<R>(p.n_media, DET ? p.n_det : 0, tile_e).total;
-    walk_kernel<R, DET, ACC, ST><<<s.grid, s.block, smem, st>>>(p);
+    const size_t smem = SmemLayout<R>(BATCH ? 0 : p.n_media, DET ? p.n_det : 0, tile_e).total;
+    walk_kernel<R, DET, ACC, ST, BATCH><<<s.grid, s.block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -796,6 +866,18 @@ cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const La
 {
     if (prec == Precision::F64) return launch_a<double>(p, accum, s, st);
     return launch_a<float>(p, accum, s, st);
+}
+
+cudaError_t walk_batch_query_shape(int accum, int block, LaunchShape *shape)
+{
+    if (accum == kAccF64) return shape_for<float, false, kAccF64, false, true>(block, 0, 0, 0, shape);
+    return shape_for<float, false, kAccPlain, false, true>(block, 0, 0, 0, shape);
+}
+
+cudaError_t walk_batch_launch(const WalkParams &p, int accum, const LaunchShape &s, cudaStream_t st)
+{
+    if (accum == kAccF64) return launch<float, false, kAccF64, false, true>(p, s, st);
+    return launch<float, false, kAccPlain, false, true>(p, s, st);
 }
 
 cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out)

@@ -1,0 +1,135 @@
+"""Batched simulations: many problems in one persistent launch.
+
+A simulation's photon p draws the stream of (its seed, p), so each member of a batch
+reproduces the same simulation run alone through mcx_run photon by photon.  The batch
+walk is a separately compiled FP32 instantiation of the kernel, so rounding (FMA
+contraction) can differ in the last bit and a few chaotic trajectories part ways; the
+members therefore agree with their standalone runs to ~1e-6 in the tallies and ~1e-4 in
+relative L2 of the map, far inside Monte Carlo noise.  The C4 batch (256 uneven volumes)
+checks scale: every photon is simulated and every member's energy balances.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_common import F32_RR, balance, f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    from paper_1711_03244_gb300 import build
+    build.build()
+    import paper_1711_03244_gb300 as m
+    m.load()
+    return m
+
+
+def _members():
+    sims = [f32(w) for w in workloads.c4(n_sims=6)]
+    sims = [w.with_(n_photons=min(w.n_photons, 60_000)) for w in sims]
+    sims.append(f32(workloads.c1(n_photons=40_000)).with_(n_gates=5, dt_ns=1.0, seed=77))
+    sims.append(f32(workloads.c3(n_photons=3_000)).with_(labels=workloads.c3().labels[:40, 100:156, 100:156].copy(),
+                                                      src_pos=(14.0, 14.0, 0.0), n_gates=5,
+                                                      dt_ns=1.0, seed=5))
+    sims.append(f32(workloads.c1(n_photons=0)).with_(n_gates=5, dt_ns=1.0, seed=9))
+    return sims
+
+
+def _alone(g, wl):
+    with g.Simulation.from_workload(wl.with_(detectors=np.zeros((0, 4)))) as sim:
+        sim.run(wl.n_photons, n_gates=5, dt_ns=1.0, seed=wl.seed, rr_threshold=F32_RR)
+        return sim.fluence64(), sim.tally()
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_members_equal_standalone_runs(g, use_graph):
+    sims = _members()
+    with g.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl)
+        for rep in range(2):                      # the second run replays the graph
+            b.run(n_gates=5, dt_ns=1.0, rr_threshold=F32_RR, use_graph=use_graph)
+            stats = b.stats()
+            assert stats["photons"] == sum(w.n_photons for w in sims)
+            for i, wl in enumerate(sims):
+                E_alone, t_alone = _alone(g, wl)
+                t = b.tally(i)
+                n = max(wl.n_photons, 1)
+                for k in t:
+                    assert abs(t[k] - t_alone[k]) <= 1e-5 * n, (i, k, t[k], t_alone[k])
+                E = b.fluence(i).astype(np.float64)
+                if wl.n_photons:
+                    l2 = np.linalg.norm(E - E_alone) / np.linalg.norm(E_alone)
+                    print(f"member {i}: map L2 vs standalone {l2:.1e}, absorbed "
+                          f"{t['absorbed']:.6f} vs {t_alone['absorbed']:.6f}")
+                    assert l2 < 1e-3, i
+                    assert abs(balance(t) - wl.n_photons) <= 1e-6 * wl.n_photons
+                else:
+                    assert not E.any()
+
+
+def test_batch_fp32_accumulation_and_normalisation(g):
+    sims = _members()[:3]
+    with g.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl)
+        b.run(n_gates=5, dt_ns=1.0, rr_threshold=F32_RR, accum_mode=0)
+        for i, wl in enumerate(sims):
+            E_alone, _ = _alone(g, wl)
+            E = b.fluence(i).astype(np.float64)
+            assert np.linalg.norm(E - E_alone) / np.linalg.norm(E_alone) < 1e-3
+            Phi = b.fluence(i, normalized=True).astype(np.float64)
+            mua = wl.media[:, 0].astype(np.float32).astype(np.float64)[wl.labels]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                expect = E / (mua * wl.voxel_mm ** 3 * wl.n_photons * 1.0)
+            expect[:, mua == 0] = 0
+            assert np.allclose(Phi, expect, rtol=1e-5, atol=0)
+
+
+def test_batch_autotune_picks_a_valid_shape(g):
+    sims = [f32(w) for w in workloads.c4(n_sims=12)]
+    with g.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl, n_photons=min(wl.n_photons, 200_000))
+        best = b.autotune(fraction=0.25, n_gates=5, dt_ns=1.0)
+        assert best["block_size"] in (128, 256) and best["claim_chunk"] in (32, 64, 128, 256)
+        assert best["ms"] > 0
+        b.run(n_gates=5, dt_ns=1.0, block_size=best["block_size"], claim_chunk=best["claim_chunk"])
+        for i in range(len(sims)):
+            t = b.tally(i)
+            assert abs(balance(t) - t["launched"]) <= 1e-6 * max(t["launched"], 1)
+
+
+def test_batch_rejects_bad_input(g):
+    with g.Batch() as b:
+        with pytest.raises(g.McxError):
+            b.run(n_gates=5, dt_ns=1.0)                          # empty batch
+        wl = workloads.c1(n_photons=10)
+        with pytest.raises(g.McxError):
+            b.add(np.full((4, 4, 4), 5, np.uint8), 1.0, wl.media, n_photons=10)   # label 5
+        b.add_workload(wl)
+        with pytest.raises(g.McxError):
+            b.run(n_gates=5, dt_ns=1.0, accum_mode=1)            # not in batches
+        with pytest.raises(g.McxError):
+            b.run(n_gates=5, dt_ns=1.0, claim_chunk=16)
+
+
+def test_c4_batch_256_simulations(g):
+    sims = workloads.c4()
+    total = sum(w.n_photons for w in sims)
+    with g.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl)
+        b.run(n_gates=5, dt_ns=1.0, use_graph=1)
+        ms = b.last_ms()
+        st = b.stats()
+        assert st["photons"] == total
+        worst = 0.0
+        for i, wl in enumerate(sims):
+            t = b.tally(i)
+            worst = max(worst, abs(balance(t) - wl.n_photons) / wl.n_photons)
+        print(f"c4: {len(sims)} simulations, {total:.3e} photons in {ms:.0f} ms "
+              f"= {total / ms:.0f} photons/ms; worst energy balance {worst:.1e}")
+        assert worst < 1e-5
