@@ -37,9 +37,26 @@ enum { EV_FACE = 0, EV_SCAT = 1, EV_TIME = 2 };
 
 // ------------------------------------------------------------------------------ math
 template <typename R> struct M;
+// The FP32 walk keeps hop lengths in units of ln 2 mean free paths and its absorption
+// coefficients multiplied by log2(e) (the per-label tables are scaled to match), so a hop
+// is one lg2 and an attenuation one ex2 on the special-function unit; the FP64 walk uses
+// natural units and the library log/exp.
 template <> struct M<float> {
     static __device__ __forceinline__ float log(float x) { return __logf(x); }
-    static __device__ __forceinline__ float exp(float x) { return __expf(x); }
+    static __device__ __forceinline__ float hop(float u)
+    {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(u));
+        return -y;
+    }
+    static __device__ __forceinline__ float attenuation(float a, float l)
+    {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-a * l));
+        return y;
+    }
+    static constexpr double kHopUnit = 0.69314718055994530942;     // ln 2
+    static constexpr double kAbsScale = 1.44269504088896340736;    // log2(e)
     static __device__ __forceinline__ void sincos_2pi(float x, float *s, float *c)
     { __sincosf(6.28318530717958647692f * x, s, c); }
     static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
@@ -50,7 +67,10 @@ template <> struct M<float> {
 };
 template <> struct M<double> {
     static __device__ __forceinline__ double log(double x) { return ::log(x); }
-    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double hop(double u) { return -::log(u); }
+    static __device__ __forceinline__ double attenuation(double a, double l) { return ::exp(-a * l); }
+    static constexpr double kHopUnit = 1.0;
+    static constexpr double kAbsScale = 1.0;
     static __device__ __forceinline__ void sincos_2pi(double x, double *s, double *c)
     { ::sincospi(2.0 * x, s, c); }
     static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
@@ -60,7 +80,7 @@ template <> struct M<double> {
     static __device__ __forceinline__ double tiny_hop() { return 1e-300; }
 };
 
-// Per-label tables in the walk's precision.
+// Per-label tables in the walk's precision (FP32: mus and mua in the scaled units above).
 template <typename R> struct MedA { R mus, inv_mus, mua, len_per_t; };
 template <typename R> struct MedB { R one_m_g, one_p_g, one_m_g2, two_g; };
 
@@ -342,7 +362,7 @@ walk_kernel(const WalkParams p)
     };
     // a4: dimensionless hop in mean free paths
     auto new_hop = [&]() {
-        const R h = -M<R>::log(R(rng.uniform()));
+        const R h = M<R>::hop(R(rng.uniform()));
         s = h > M<R>::tiny_hop() ? h : M<R>::tiny_hop();
     };
 
@@ -497,7 +517,7 @@ walk_kernel(const WalkParams p)
             t += l * med_tpl(lab);
             s = ev == EV_SCAT ? R(0) : s - l * A.mus;
             if (DET) Lcur += l;
-            const R wn = w * M<R>::exp(-A.mua * l);
+            const R wn = w * M<R>::attenuation(A.mua, l);
             const R dw = w - wn;
             w = wn;
             absorbed += dw;
@@ -508,72 +528,81 @@ walk_kernel(const WalkParams p)
             } else if (ev == EV_FACE) {
                 // ---- a8: voxel face
                 ++c_face;
-                const R ua = ax == 0 ? ux : (ax == 1 ? uy : uz);
-                const bool up = ua >= R(0);
-                const R qb = up ? R(1) : R(0);
-                const int ia = (ax == 0 ? ix : (ax == 1 ? iy : iz)) + (up ? 1 : -1);
-                const int dim = ax == 0 ? G_nx : (ax == 1 ? G_ny : G_nz);
-                const unsigned stride = ax == 0 ? 1u : (ax == 1 ? (unsigned)G_nx : nxy);
+                const bool p0 = ax == 0, p1 = ax == 1;
+                const R inv_a = p0 ? iux : (p1 ? iuy : iuz);
+                const bool up = inv_a > R(0);              // u_ax >= 0 (inv_dir of 0 is +huge)
+                const int ia = (p0 ? ix : (p1 ? iy : iz)) + (up ? 1 : -1);
+                const int dim = p0 ? G_nx : (p1 ? G_ny : G_nz);
+                const unsigned stride = p0 ? 1u : (p1 ? (unsigned)G_nx : nxy);
                 const unsigned nlin = up ? vlin + stride : vlin - stride;
                 const bool inside = (unsigned)ia < (unsigned)dim;
                 const int b = inside ? (int)__ldg(G_labels + nlin) : 0;
-                // photon on the face
-                qx = ax == 0 ? qb : qx;
-                qy = ax == 1 ? qb : qy;
-                qz = ax == 2 ? qb : qz;
-                bool enter = false, escape = false;
                 if (b == lab) {
-                    enter = true;
-                } else if (!p.reflect) {
-                    // the paper's B1: the exterior terminates, internal mismatches pass
-                    if (b == 0) escape = true; else enter = true;
+                    // same medium: straight into the next voxel, entering on the near face
+                    flush();                              // the deposit run ends with the voxel
+                    const R qn = up ? R(0) : R(1);
+                    if (p0) { ix = ia; qx = qn; } else if (p1) { iy = ia; qy = qn; } else { iz = ia; qz = qn; }
+                    vlin = nlin;
+                    if (s <= R(0)) new_hop();            // hop used up by rounding at the face
                 } else {
-                    const R na = med_n(lab), nb = med_n(b);
-                    if (na == nb) {
+                    // photon on the face
+                    const R qb = up ? R(1) : R(0);
+                    qx = p0 ? qb : qx;
+                    qy = p1 ? qb : qy;
+                    qz = !p0 && !p1 ? qb : qz;
+                    const R ua = p0 ? ux : (p1 ? uy : uz);
+                    bool enter = false, escape = false;
+                    if (!p.reflect) {
+                        // the paper's B1: the exterior terminates, internal mismatches pass
                         if (b == 0) escape = true; else enter = true;
                     } else {
-                        ++c_fres;
-                        const R ci = fabs(ua);
-                        const R eta = M<R>::div(na, nb);
-                        const R st2 = eta * eta * (R(1) - ci * ci);
-                        bool refl = true;                 // total internal reflection
-                        if (st2 < R(1)) refl = R(rng.uniform()) < fresnel(na, nb, ci, st2);
-                        if (refl) {
-                            ux = ax == 0 ? -ux : ux;
-                            uy = ax == 1 ? -uy : uy;
-                            uz = ax == 2 ? -uz : uz;
-                            iux = ax == 0 ? -iux : iux;
-                            iuy = ax == 1 ? -iuy : iuy;
-                            iuz = ax == 2 ? -iuz : iuz;
-                        } else {
-                            // Snell: tangential components x eta, normal = +-cos(theta_t)
-                            const R ctt = M<R>::sqrt(R(1) - st2);
-                            const R un = up ? ctt : -ctt;
-                            ux = ax == 0 ? un : ux * eta;
-                            uy = ax == 1 ? un : uy * eta;
-                            uz = ax == 2 ? un : uz * eta;
-                            iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
+                        const R na = med_n(lab), nb = med_n(b);
+                        if (na == nb) {
                             if (b == 0) escape = true; else enter = true;
+                        } else {
+                            ++c_fres;
+                            const R ci = fabs(ua);
+                            const R eta = M<R>::div(na, nb);
+                            const R st2 = eta * eta * (R(1) - ci * ci);
+                            bool refl = true;                 // total internal reflection
+                            if (st2 < R(1)) refl = R(rng.uniform()) < fresnel(na, nb, ci, st2);
+                            if (refl) {
+                                ux = p0 ? -ux : ux;
+                                uy = p1 ? -uy : uy;
+                                uz = !p0 && !p1 ? -uz : uz;
+                                iux = p0 ? -iux : iux;
+                                iuy = p1 ? -iuy : iuy;
+                                iuz = !p0 && !p1 ? -iuz : iuz;
+                            } else {
+                                // Snell: tangential components x eta, normal = +-cos(theta_t)
+                                const R ctt = M<R>::sqrt(R(1) - st2);
+                                const R un = up ? ctt : -ctt;
+                                ux = p0 ? un : ux * eta;
+                                uy = p1 ? un : uy * eta;
+                                uz = !p0 && !p1 ? un : uz * eta;
+                                iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
+                                if (b == 0) escape = true; else enter = true;
+                            }
                         }
                     }
-                }
-                if (enter) {
-                    flush();                              // the deposit run ends with the voxel
-                    ix = ax == 0 ? ia : ix;
-                    iy = ax == 1 ? ia : iy;
-                    iz = ax == 2 ? ia : iz;
-                    qx = ax == 0 ? R(1) - qb : qx;
-                    qy = ax == 1 ? R(1) - qb : qy;
-                    qz = ax == 2 ? R(1) - qb : qz;
-                    vlin = nlin;
-                    if (DET && b != lab) {
-                        if (lab < kMaxDetMedia) Lpath[lab] += float(Lcur);
-                        Lcur = R(0);
+                    if (enter) {
+                        flush();
+                        ix = p0 ? ia : ix;
+                        iy = p1 ? ia : iy;
+                        iz = !p0 && !p1 ? ia : iz;
+                        qx = p0 ? R(1) - qb : qx;
+                        qy = p1 ? R(1) - qb : qy;
+                        qz = !p0 && !p1 ? R(1) - qb : qz;
+                        vlin = nlin;
+                        if (DET) {
+                            if (lab < kMaxDetMedia) Lpath[lab] += float(Lcur);
+                            Lcur = R(0);
+                        }
+                        lab = b;
                     }
-                    lab = b;
+                    if (escape) fate = MCX_FATE_ESCAPED;
+                    else if (s <= R(0)) new_hop();        // hop used up by rounding at the face
                 }
-                if (escape) fate = MCX_FATE_ESCAPED;
-                else if (s <= R(0)) new_hop();            // hop used up by rounding at the face
             } else {
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
@@ -741,9 +770,11 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
         const R mua = R(props[4 * m]), mus = R(props[4 * m + 1]);
         const R g = R(props[4 * m + 2]), nn = R(props[4 * m + 3]);
         MedA<R> A;
-        A.mus = mus * hh;
-        A.inv_mus = A.mus > R(0) ? R(1) / A.mus : R(INFINITY);
-        A.mua = mua * hh;
+        // scattering and absorption per voxel length, in the walk's units (M<R>)
+        const double mus_v = (double)mus * (double)hh, mua_v = (double)mua * (double)hh;
+        A.mus = R(mus_v / M<R>::kHopUnit);
+        A.inv_mus = mus_v > 0 ? R(M<R>::kHopUnit / mus_v) : R(INFINITY);
+        A.mua = R(mua_v * M<R>::kAbsScale);
         A.len_per_t = c0 / (nn * hh);
         MedB<R> B;
         B.one_m_g = R(1) - g;
