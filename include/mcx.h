@@ -313,6 +313,73 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
                            float waist_mm, const mcx_run_cfg *cfg, float *fluence_dev,
                            double *tally_dev);
 
+/* ---- learned denoiser -----------------------------------------------------------------
+   The paper has no counterpart: this extends the method with a small 3-D convolutional
+   network that maps the fluence of a low-photon run to an estimate of a high-photon run's,
+   so that fewer photons reach a given voxel-wise error.  A plain run with more photons
+   stays the fallback: the denoiser never replaces the walk, it post-processes its map.
+
+   Network (a U-Net; all 3x3x3 convolutions have a bias and ReLU, "same" zero padding):
+     level 0 (nz,ny,nx):   e1a 1->16 (the input channel zero-padded to 16), e1b 16->16
+     2x2x2 average pool;   level 1: e2a 16->32, e2b 32->32
+     2x2x2 average pool;   level 2: ba 32->64, bb 64->64
+     nearest x2 upsample, concatenated with e2b's output (upsampled channels first):
+                           level 1: d2a 96->32, d2b 32->32
+     nearest x2 upsample, concatenated with e1b's output: level 0: d1a 48->16, d1b 16->16
+     head: y = x + hb + sum_c hw[c] * d1b[c]   (1x1x1, FP32)
+   Weights and activations are BF16, every convolution accumulates in FP32 on tensor
+   cores; master weights, gradients and the Adam state are FP32.
+
+   Parameters are one FP32 vector, layer by layer in the order above: for each of the ten
+   convolutions its weights [27 taps][cout][cin] (tap = 9 (dz+1) + 3 (dy+1) + (dx+1), the
+   input read at (z+dz, y+dy, x+dx)) then its bias [cout]; then hw[16], then hb.
+   The network domain: x = (log10(max(phi, 0) + floor) - mu) / sigma, with the inverse
+   phi = max(10^(x sigma + mu) - floor, 0); defaults floor 1e-8, mu -4, sigma 2.
+
+   Volumes are FP32 [n][nz][ny][nx] device arrays on the denoiser's device, n <= max_batch.
+   Sizes: nx a multiple of 64, ny and nz multiples of 4.  The object owns every buffer it
+   needs (activations for max_batch volumes); calls on one object must not overlap.
+   Errors: MCX_E_ARG (bad sizes or NULL), MCX_E_OOM, MCX_E_CUDA, described by
+   mcx_last_error(NULL). */
+typedef struct mcx_denoiser mcx_denoiser;
+
+/* He-normal weights drawn from `seed`, zero biases and a zero head (the untrained network
+   returns its input). */
+mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uint32_t nz,
+                               uint32_t max_batch, uint64_t seed);
+mcx_status mcx_denoiser_param_count(const mcx_denoiser *d, uint64_t *n);
+/* which = 0: the FP32 master weights; which = 1: the gradients of the last train step.
+   Waits for the device. */
+mcx_status mcx_denoiser_get_params(mcx_denoiser *d, float *host, uint64_t n, int32_t which);
+/* Replaces the weights (and resets the optimizer state). Waits for the device. */
+mcx_status mcx_denoiser_set_params(mcx_denoiser *d, const float *host, uint64_t n);
+mcx_status mcx_denoiser_set_encoding(mcx_denoiser *d, float floor_, float mu, float sigma);
+/* Network domain in and out: y_dev = net(x_dev) for n volumes, enqueued on `stream`. */
+mcx_status mcx_denoiser_forward(mcx_denoiser *d, const float *x_dev, float *y_dev, uint32_t n,
+                                void *stream);
+/* One training step on n (input, target) pairs in the network domain: loss = mean over all
+   voxels of (net(x) - t)^2, gradients of every parameter, then (if lr > 0) one Adam step
+   (beta 0.9 / 0.999, eps 1e-8).  With loss_host non-NULL the call waits and returns the
+   loss there. */
+mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const float *t_dev,
+                                   uint32_t n, float lr, float *loss_host, void *stream);
+/* Elementwise maps between fluence and the network domain (count values). */
+mcx_status mcx_denoiser_encode(mcx_denoiser *d, const float *phi_dev, float *x_dev,
+                               uint64_t count, void *stream);
+mcx_status mcx_denoiser_decode(mcx_denoiser *d, const float *x_dev, float *phi_dev,
+                               uint64_t count, void *stream);
+/* Denoises n fluence maps: encode, forward, decode, enqueued on `stream`. */
+mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, float *phi_out_dev,
+                              uint32_t n, void *stream);
+/* Builds a training batch: volume s of dst_dev (n volumes) is volume idx[s] of set_dev
+   (set_count volumes of the denoiser's shape), mirrored in x (flags[s] bit 0) and in y
+   (bit 1), then transposed in x/y (bit 2; needs ny == nx).  idx and flags are host arrays
+   of n <= 64 entries, read before the call returns. */
+mcx_status mcx_denoiser_gather(mcx_denoiser *d, const float *set_dev, uint64_t set_count,
+                               const uint64_t *idx, const uint32_t *flags, uint32_t n,
+                               float *dst_dev, void *stream);
+void mcx_denoiser_destroy(mcx_denoiser *d);
+
 /* ---- diagnostics: run the library's device primitives on small host arrays ---------- */
 
 /* Photon `photon`'s stream for `seed`, as the walk kernel draws it: for each of the first
@@ -326,6 +393,17 @@ mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float 
      kind 2: Fresnel reflectance,       in (n1, n2, cos_i)                     -> out (R; 1 on TIR) */
 mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
                                float *out_host);
+
+/* One tensor-core 3x3x3 convolution of the denoiser on host arrays (values rounded to
+   BF16 on the way in), n volumes of nz x ny x nx, nx a multiple of 16:
+     kind 0: forward,  x [n][nz][ny][nx][cin], w [27][cout][cin], bias [cout] or NULL
+             -> out = ReLU(conv + bias) [n][nz][ny][nx][cout], rounded to BF16
+     kind 1: weight gradient, x as above, dy [n][nz][ny][nx][cout]
+             -> out [27][cout][cin] = sum over positions of dy * x(shifted by the tap), FP32
+   cin and cout from {16, 32, 48, 64, 96}. */
+mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t nz, int32_t ny, int32_t nx,
+                            int32_t cin, int32_t cout, const float *x, const float *w,
+                            const float *bias, const float *dy, float *out);
 
 #ifdef __cplusplus
 }

@@ -136,8 +136,21 @@ SIGNATURES = {
     "mcx_batch_size": (_i32, [_P]),
     "mcx_batch_last_error": (ctypes.c_char_p, [_P]),
     "mcx_batch_destroy": (None, [_P]),
+    "mcx_denoiser_create": (_i32, [ctypes.POINTER(_P), _u32, _u32, _u32, _u32, _u64]),
+    "mcx_denoiser_param_count": (_i32, [_P, ctypes.POINTER(_u64)]),
+    "mcx_denoiser_get_params": (_i32, [_P, _P, _u64, _i32]),
+    "mcx_denoiser_set_params": (_i32, [_P, _P, _u64]),
+    "mcx_denoiser_set_encoding": (_i32, [_P, _f32, _f32, _f32]),
+    "mcx_denoiser_forward": (_i32, [_P, _P, _P, _u32, _P]),
+    "mcx_denoiser_train_step": (_i32, [_P, _P, _P, _u32, _f32, ctypes.POINTER(_f32), _P]),
+    "mcx_denoiser_encode": (_i32, [_P, _P, _P, _u64, _P]),
+    "mcx_denoiser_decode": (_i32, [_P, _P, _P, _u64, _P]),
+    "mcx_denoiser_apply": (_i32, [_P, _P, _P, _u32, _P]),
+    "mcx_denoiser_gather": (_i32, [_P, _P, _u64, _P, _P, _u32, _P, _P]),
+    "mcx_denoiser_destroy": (None, [_P]),
     "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
     "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
+    "mcx_debug_conv3d": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -359,6 +372,28 @@ def mcx_debug_primitive(kind: int, inputs: np.ndarray) -> np.ndarray:
     return out if nout > 1 else out[:, 0]
 
 
+def mcx_debug_conv3d(kind: int, x: np.ndarray, w=None, bias=None, dy=None, cout=None) -> np.ndarray:
+    """One denoiser convolution on host arrays: x [n, nz, ny, nx, cin] (channels last).
+    kind 0: w [27, cout, cin], bias [cout] or None -> ReLU(conv + bias), BF16-rounded
+    kind 1: dy [n, nz, ny, nx, cout] -> weight gradient [27, cout, cin]"""
+    xa = np.ascontiguousarray(x, dtype=np.float32)
+    n, nz, ny, nx, cin = xa.shape
+    if kind == 0:
+        wa = np.ascontiguousarray(w, dtype=np.float32)
+        cout = wa.shape[1]
+        ba = None if bias is None else np.ascontiguousarray(bias, dtype=np.float32)
+        out = np.zeros((n, nz, ny, nx, cout), dtype=np.float32)
+        _check(None, load().mcx_debug_conv3d(0, n, nz, ny, nx, cin, cout, _ptr(xa), _ptr(wa),
+                                             _ptr(ba), None, _ptr(out)))
+    else:
+        da = np.ascontiguousarray(dy, dtype=np.float32)
+        cout = da.shape[-1]
+        out = np.zeros((27, cout, cin), dtype=np.float32)
+        _check(None, load().mcx_debug_conv3d(1, n, nz, ny, nx, cin, cout, _ptr(xa), None, None,
+                                             _ptr(da), _ptr(out)))
+    return out
+
+
 def decode_detected(rec: np.ndarray) -> dict:
     """Splits uint32 record words into named fields (see include/mcx.h)."""
     f = rec.view(np.float32)
@@ -555,6 +590,110 @@ class Simulation:
     def close(self):
         if self.handle:
             mcx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Denoiser:
+    """The learned fluence denoiser (mcx_denoiser_* in include/mcx.h).  Volumes are torch
+    CUDA tensors of shape [n, nz, ny, nx] (float32, contiguous); the stream defaults to
+    torch's current stream."""
+
+    def __init__(self, shape, max_batch: int = 1, seed: int = 0):
+        nz, ny, nx = shape
+        h = ctypes.c_void_p()
+        _check(None, load().mcx_denoiser_create(ctypes.byref(h), nx, ny, nz, max_batch, seed))
+        self.handle = h
+        self.shape = (nz, ny, nx)
+        self.max_batch = max_batch
+        n = ctypes.c_uint64()
+        _check(None, load().mcx_denoiser_param_count(self.handle, ctypes.byref(n)))
+        self.n_params = n.value
+
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return ctypes.c_void_p(_stream_handle(stream))
+
+    def _vol(self, t):
+        if not (getattr(t, "is_cuda", False) and t.is_contiguous() and t.shape[1:] == self.shape
+                and str(t.dtype) == "torch.float32"):
+            raise ValueError(f"need a contiguous float32 CUDA tensor [n, {self.shape}]")
+        return t.shape[0]
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(None, load().mcx_denoiser_get_params(self.handle, _ptr(out), self.n_params, 0))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(None, load().mcx_denoiser_get_params(self.handle, _ptr(out), self.n_params, 1))
+        return out
+
+    def set_params(self, p: np.ndarray):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check(None, load().mcx_denoiser_set_params(self.handle, _ptr(a), self.n_params))
+
+    def set_encoding(self, floor: float, mu: float, sigma: float):
+        _check(None, load().mcx_denoiser_set_encoding(self.handle, floor, mu, sigma))
+
+    def forward(self, x, y, stream=None):
+        n = self._vol(x)
+        self._vol(y)
+        _check(None, load().mcx_denoiser_forward(self.handle, _ptr(x), _ptr(y), n, self._stream(stream)))
+
+    def train_step(self, x, t, lr: float, stream=None) -> float:
+        n = self._vol(x)
+        self._vol(t)
+        loss = ctypes.c_float()
+        _check(None, load().mcx_denoiser_train_step(self.handle, _ptr(x), _ptr(t), n, lr,
+                                                    ctypes.byref(loss), self._stream(stream)))
+        return loss.value
+
+    def encode(self, phi, x, stream=None):
+        _check(None, load().mcx_denoiser_encode(self.handle, _ptr(phi), _ptr(x), phi.numel(),
+                                                self._stream(stream)))
+
+    def decode(self, x, phi, stream=None):
+        _check(None, load().mcx_denoiser_decode(self.handle, _ptr(x), _ptr(phi), x.numel(),
+                                                self._stream(stream)))
+
+    def apply(self, phi_in, phi_out, stream=None):
+        n = self._vol(phi_in)
+        self._vol(phi_out)
+        _check(None, load().mcx_denoiser_apply(self.handle, _ptr(phi_in), _ptr(phi_out), n,
+                                               self._stream(stream)))
+
+    def gather(self, volumes, idx, flags, out, stream=None):
+        """out[s] = transformed volumes[idx[s]] (see mcx_denoiser_gather)"""
+        i = np.ascontiguousarray(idx, dtype=np.uint64)
+        f = np.ascontiguousarray(flags, dtype=np.uint32)
+        if i.size != f.size or out.shape[0] != i.size:
+            raise ValueError("idx, flags and out must agree in length")
+        self._vol(volumes)
+        self._vol(out)
+        _check(None, load().mcx_denoiser_gather(self.handle, _ptr(volumes), volumes.shape[0], _ptr(i),
+                                                _ptr(f), i.size, _ptr(out), self._stream(stream)))
+
+    def close(self):
+        if self.handle:
+            load().mcx_denoiser_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -176,6 +176,32 @@ def c4(n_sims: int = 256, seed: int = 1711032440) -> List[Workload]:
     return out
 
 
+def c5(n_volumes: int, seed: int, n_photons: int = 100_000) -> List[Workload]:
+    """Seeded 64 mm cubes for the learned denoiser, drawn like c4 with the side fixed at
+    64: 1-3 random axis-aligned ellipsoids, random optical properties, pencil source at a
+    random point of the z=0 face, one 0-5 ns gate.  Disjoint seeds give disjoint training
+    and held-out sets; the simulation seed of volume k is seed + 1 + k."""
+    rng = np.random.default_rng(seed)
+    side = 64
+    out = []
+    for k in range(n_volumes):
+        n_inc = int(rng.integers(1, 4))
+        labels = np.ones((side, side, side), dtype=np.uint8)
+        rows = [AIR]
+        for _ in range(n_inc + 1):
+            rows.append((float(10 ** rng.uniform(-3, -1)), float(rng.uniform(0.5, 20.0)),
+                         float(rng.uniform(0.5, 0.95)), float(rng.uniform(1.33, 1.45))))
+        for i in range(n_inc):
+            centre = rng.uniform(0.2 * side, 0.8 * side, size=3)
+            semi = rng.uniform(0.1 * side, 0.3 * side, size=3)
+            paint_ellipsoid(labels, 1.0, tuple(centre), tuple(semi), i + 2)
+        sx, sy = rng.uniform(0.0, side, size=2)
+        out.append(Workload(f"c5_vol{k:04d}", labels, 1.0, np.array(rows, dtype=np.float64), 0,
+                            (float(sx), float(sy), 0.0), (0.0, 0.0, 1.0), 0.0, np.zeros((0, 4)),
+                            n_photons, 1, 5.0, 1, seed + 1 + k))
+    return out
+
+
 def paper_b(variant: str = "B1", n_photons: int = 100_000_000, seed: int = 12345) -> Workload:
     """The paper's benchmarks: 60 mm cube (mua 0.005, mus 1.0, g 0.01, n 1.37) in air,
     pencil beam at (30,30,0) +z.  B2/B2a add a central r=15 mm sphere (mua 0.002, mus 5.0,
