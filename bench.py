@@ -336,6 +336,7 @@ def study_denoise(args):
         dn.denoise(d, low_in, out)
     e1.record()
     e1.synchronize()
+    d.sync()
     apply_ms = e0.elapsed_time(e1) / reps
     oh = out.cpu().numpy()
     den_rms = float(np.mean([dn.log_rms(oh[i], ref_h[i]) for i in range(n_t)]))
@@ -379,6 +380,51 @@ def study_denoise(args):
     d.close()
 
 
+def study_denoise_kernels(args):
+    """The denoiser's kernels alone on synthetic inputs: one forward pass over 16 volumes of
+    64^3 (every 3x3x3 convolution on tcgen05) and one training step of batch 4, each the
+    median of args.steps timed repetitions after args.warmup untimed ones (CUDA events)."""
+    import torch
+    import paper_1711_03244_gb300 as mcx
+    from paper_1711_03244_gb300 import build as mcx_build
+    mcx_build.build()
+    mcx.load()
+    shape, nb = (64, 64, 64), 16
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn((nb,) + shape, device="cuda", generator=g)
+    t = x + 0.1 * torch.randn((nb,) + shape, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    npos = [64 ** 3, 64 ** 3, 32 ** 3, 32 ** 3, 16 ** 3, 16 ** 3, 32 ** 3, 32 ** 3, 64 ** 3, 64 ** 3]
+    chans = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
+    fwd = sum(2 * p * 27 * ci * co for p, (ci, co) in zip(npos, chans))
+    # a training step: forward, input gradients of every layer but the first, weight gradients
+    dgrad = fwd - 2 * npos[0] * 27 * 16 * 16
+    with mcx.Denoiser(shape, max_batch=nb, seed=1) as d:
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            d.sync()
+            return float(np.median(ms))
+        f_ms = timed(lambda: d.forward(x, y))
+        t_ms = timed(lambda: d.train_step(x[:4], t[:4], 1e-4))
+    pk = peaks()
+    f_tf = fwd * nb / (f_ms * 1e-3) / 1e12
+    t_tf = (fwd + dgrad + fwd) * 4 / (t_ms * 1e-3) / 1e12
+    print(json.dumps({"study": "denoise-kernels", "volumes": f"{nb} x 64^3 forward, 4 x 64^3 train",
+                      "forward_ms": f_ms, "forward_gflop_per_volume": fwd / 1e9,
+                      "forward_tflops": f_tf, "train_step_ms": t_ms, "train_tflops": t_tf,
+                      "bf16_peak_tflops": pk["bf16_tflops"],
+                      "forward_frac_of_peak": f_tf / pk["bf16_tflops"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,12 +438,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-model", action="store_true",
                     help="skip the pilot runs of the linear runtime model T = a n + T0")
-    ap.add_argument("--study", default=None, choices=["paper", "batched", "denoise"],
+    ap.add_argument("--study", default=None, choices=["paper", "batched", "denoise", "denoise-kernels"],
                     help="paper: the paper's benchmarks B1/B2/B2a under each accumulation and "
                          "photon-distribution mode; batched: the 256-simulation batch in one "
                          "launch vs one launch per simulation; denoise: train the learned "
-                         "denoiser and compare denoised and plain runs at equal error "
-                         "(one JSON line each)")
+                         "denoiser and compare denoised and plain runs at equal error; "
+                         "denoise-kernels: the denoiser's forward pass and training step "
+                         "alone (one JSON line each)")
     ap.add_argument("--dn-train", type=int, default=512, help="training volumes")
     ap.add_argument("--dn-test", type=int, default=16, help="held-out volumes")
     ap.add_argument("--dn-in", type=int, default=100_000, help="photons of an input map")
@@ -424,6 +471,9 @@ def main():
         return
     if args.study == "denoise":
         study_denoise(args)
+        return
+    if args.study == "denoise-kernels":
+        study_denoise_kernels(args)
         return
 
     import torch

@@ -339,8 +339,8 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
    Volumes are FP32 [n][nz][ny][nx] device arrays on the denoiser's device, n <= max_batch.
    Sizes: nx a multiple of 64, ny and nz multiples of 4.  The object owns every buffer it
    needs (activations for max_batch volumes); calls on one object must not overlap.
-   Errors: MCX_E_ARG (bad sizes or NULL), MCX_E_OOM, MCX_E_CUDA, described by
-   mcx_last_error(NULL). */
+   Errors: MCX_E_ARG (bad sizes or NULL), MCX_E_OOM, MCX_E_CUDA, MCX_E_TIMEOUT (see
+   mcx_denoiser_sync), described by mcx_last_error(NULL). */
 typedef struct mcx_denoiser mcx_denoiser;
 
 /* He-normal weights drawn from `seed`, zero biases and a zero head (the untrained network
@@ -378,6 +378,10 @@ mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, float *p
 mcx_status mcx_denoiser_gather(mcx_denoiser *d, const float *set_dev, uint64_t set_count,
                                const uint64_t *idx, const uint32_t *flags, uint32_t n,
                                float *dst_dev, void *stream);
+/* Waits for the device; MCX_E_TIMEOUT if a tensor-core pipeline wait of an earlier call
+   gave up (its results are invalid; the object stays usable).  train_step with a loss
+   pointer and get_params make the same check. */
+mcx_status mcx_denoiser_sync(mcx_denoiser *d);
 void mcx_denoiser_destroy(mcx_denoiser *d);
 
 /* ---- diagnostics: run the library's device primitives on small host arrays ---------- */
@@ -394,8 +398,9 @@ mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float 
 mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
                                float *out_host);
 
-/* One tensor-core 3x3x3 convolution of the denoiser on host arrays (values rounded to
-   BF16 on the way in), n volumes of nz x ny x nx, nx a multiple of 16:
+/* One 3x3x3 convolution of the denoiser on host arrays, run by the denoiser's own
+   tensor-core kernels (tcgen05 for kind 0, warp-level mma for kind 1); values are rounded
+   to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16:
      kind 0: forward,  x [n][nz][ny][nx][cin], w [27][cout][cin], bias [cout] or NULL
              -> out = ReLU(conv + bias) [n][nz][ny][nx][cout], rounded to BF16
      kind 1: weight gradient, x as above, dy [n][nz][ny][nx][cout]

@@ -147,6 +147,7 @@ SIGNATURES = {
     "mcx_denoiser_decode": (_i32, [_P, _P, _P, _u64, _P]),
     "mcx_denoiser_apply": (_i32, [_P, _P, _P, _u32, _P]),
     "mcx_denoiser_gather": (_i32, [_P, _P, _u64, _P, _P, _u32, _P, _P]),
+    "mcx_denoiser_sync": (_i32, [_P]),
     "mcx_denoiser_destroy": (None, [_P]),
     "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
     "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
@@ -383,7 +384,7 @@ def mcx_debug_conv3d(kind: int, x: np.ndarray, w=None, bias=None, dy=None, cout=
         cout = wa.shape[1]
         ba = None if bias is None else np.ascontiguousarray(bias, dtype=np.float32)
         out = np.zeros((n, nz, ny, nx, cout), dtype=np.float32)
-        _check(None, load().mcx_debug_conv3d(0, n, nz, ny, nx, cin, cout, _ptr(xa), _ptr(wa),
+        _check(None, load().mcx_debug_conv3d(kind, n, nz, ny, nx, cin, cout, _ptr(xa), _ptr(wa),
                                              _ptr(ba), None, _ptr(out)))
     else:
         da = np.ascontiguousarray(dy, dtype=np.float32)
@@ -690,6 +691,10 @@ class Denoiser:
         self._vol(out)
         _check(None, load().mcx_denoiser_gather(self.handle, _ptr(volumes), volumes.shape[0], _ptr(i),
                                                 _ptr(f), i.size, _ptr(out), self._stream(stream)))
+
+    def sync(self):
+        """waits for the device and raises McxError if a tensor-core wait timed out"""
+        _check(None, load().mcx_denoiser_sync(self.handle))
 
     def close(self):
         if self.handle:

@@ -62,65 +62,221 @@ struct Vol {
 };
 
 // ------------------------------------------------------------------------ convolution
-// Y[p][co] = act(bias[co] + sum_tap sum_ci X[p + off(tap)][ci] * W[tap][co][ci]) as an
-// implicit GEMM: M = output positions (16 per warp tile), N = Cout (8 per mma), K = Cin
-// per tap (16 per mma).  Positions outside the volume read zero (same padding).
-// Each warp owns 16 consecutive x positions of one row (W is a multiple of 16).
+// Y[p][co] = act(bias[co] + sum_tap sum_ci X[p + off(tap)][ci] * W[tap][co][ci]) (zero
+// outside the volume) as an implicit GEMM on the 5th-generation tensor cores: one CTA
+// (4 warps) computes 128 consecutive output positions x COUT channels as
+// D[128][COUT] += A_tap[128][cin] * W_tap[cin][COUT] over the 27 taps, with D in tensor
+// memory (FP32, one TMEM lane per position).  Each tap's operands are staged into shared memory by cp.async (zero-filled
+// where the tap reads outside the volume) through a 3-buffer ring; one thread issues the
+// tcgen05.mma instructions (K = 16 each) and tcgen05.commit signals an mbarrier when a
+// buffer may be refilled.  Operand layout (K-major, no swizzle, 16-byte core-matrix rows):
+// for each 16-channel slice kk, 8-row groups of two 8-channel core matrices:
+//   byte(row r, 8-channel chunk c) = (c / 2) * (rows * 32) + (r / 8) * 256 + (c % 2) * 128 + (r % 8) * 16
+// so an instruction's operand starts at slice kk with leading-dimension (K) offset 128 B and
+// stride-dimension (M/N) offset 256 B.  Every wait is bounded: on a timeout the CTA records
+// an error, still waits (bounded) for its own MMAs, frees its tensor memory and returns.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// shared-memory matrix descriptor: start, leading- and stride-dimension byte offsets,
+// descriptor version 1 (bits 46-47), no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12
+// = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTcRows = 128, kTcStages = 3, kTcHeader = 128, kTcSlack = 8192;
+
+__host__ __device__ constexpr int tc_stage_bytes(int cin, int cout) { return (kTcRows + cout) * cin * 2; }
+
+__host__ __device__ constexpr int tc_smem_bytes(int cin, int cout)
+{
+    return kTcHeader + kTcStages * tc_stage_bytes(cin, cout) + kTcSlack;
+}
+
 template <int COUT>
 __global__ void __launch_bounds__(128)
-conv3d_fwd(const bf16 *__restrict__ X, int cin, const bf16 *__restrict__ Wt,
-           const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y)
+conv3d_fwd_tc(const bf16 *__restrict__ X, int cin, const bf16 *__restrict__ Wt,
+              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const long long p0 = ((long long)blockIdx.x * 4 + warp) * 16;
-    if (p0 >= v.pos()) return;
-    // rows g and g + 8 of the tile
-    const int x0 = (int)(p0 % v.w);
-    long long r = p0 / v.w;
-    const int y = (int)(r % v.h);
-    r /= v.h;
-    const int z = (int)(r % v.d);
-    const int b = (int)(r / v.d);
-    float acc[COUT / 8][4];
-#pragma unroll
-    for (int j = 0; j < COUT / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns
+    constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t bar0 = smem_u32(smem);                     // 3 mbarriers, 8 B each
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 64);
+    unsigned char *ring = smem + kTcHeader;
+    const int a_bytes = kTcRows * cin * 2, st_bytes = tc_stage_bytes(cin, COUT);
+    const int tid = threadIdx.x, warp = tid >> 5;
 
-    for (int tap = 0; tap < 27; ++tap) {
+    const long long P = v.pos();
+    const long long p = (long long)blockIdx.x * kTcRows + tid;  // this thread's row
+    const bool valid = p < P;
+    int x = 0, y = 0, z = 0, b = 0;
+    if (valid) {
+        long long r = p;
+        x = (int)(r % v.w); r /= v.w;
+        y = (int)(r % v.h); r /= v.h;
+        z = (int)(r % v.d);
+        b = (int)(r / v.d);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(tslot)), "r"(NCOL) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8 * s) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    // stage tap `tap` into ring buffer s
+    auto stage = [&](int tap, int s) {
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int zz = z + dz, yy = y + dy;
-        if (zz < 0 || zz >= v.d || yy < 0 || yy >= v.h) continue;       // warp-uniform
-        const int xa = x0 + g + dx, xb = x0 + g + 8 + dx;
-        const bool va = xa >= 0 && xa < v.w, vb = xb >= 0 && xb < v.w;
-        const long long rowbase = (((long long)b * v.d + zz) * v.h + yy) * v.w;
-        const bf16 *Xa = X + (rowbase + xa) * cin, *Xb = X + (rowbase + xb) * cin;
-        const bf16 *Wtap = Wt + (size_t)tap * COUT * cin;
-        for (int c0 = 0; c0 < cin; c0 += 16) {
-            const unsigned a0 = va ? __ldg(reinterpret_cast<const unsigned *>(Xa + c0 + 2 * t)) : 0u;
-            const unsigned a1 = vb ? __ldg(reinterpret_cast<const unsigned *>(Xb + c0 + 2 * t)) : 0u;
-            const unsigned a2 = va ? __ldg(reinterpret_cast<const unsigned *>(Xa + c0 + 8 + 2 * t)) : 0u;
-            const unsigned a3 = vb ? __ldg(reinterpret_cast<const unsigned *>(Xb + c0 + 8 + 2 * t)) : 0u;
+        const uint32_t A = smem_u32(ring + s * st_bytes), B = A + a_bytes;
+        const int xs = x + dx, ys = y + dy, zs = z + dz;
+        const bool in = valid && xs >= 0 && xs < v.w && ys >= 0 && ys < v.h && zs >= 0 && zs < v.d;
+        const bf16 *src = in ? X + ((((long long)b * v.d + zs) * v.h + ys) * v.w + xs) * cin : X;
+        const uint32_t arow = A + (tid >> 3) * 256 + (tid & 7) * 16;
+        for (int c = 0; c < cin / 8; ++c)
+            cp_async16(arow + (c >> 1) * (kTcRows * 32) + (c & 1) * 128, src + (in ? 8 * c : 0), in ? 16u : 0u);
+        const bf16 *wt = Wt + (size_t)tap * COUT * cin;
+        for (int i = tid; i < COUT * (cin / 8); i += 128) {
+            const int co = i % COUT, c = i / COUT;
+            cp_async16(B + (c >> 1) * (COUT * 32) + (co >> 3) * 256 + (c & 1) * 128 + (co & 7) * 16,
+                       wt + (size_t)co * cin + 8 * c, 16u);
+        }
+    };
+
+    bool ok = true;
+    stage(0, 0);
+    cp_async_commit();
+    stage(1, 1);
+    cp_async_commit();
+    for (int t = 0; t < 27; ++t) {
+        cp_async_wait<1>();                    // this thread's copies of tap t have landed
+        fence_proxy_async_smem();              // make them visible to the tensor cores
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const int s = t % kTcStages;
+            const uint32_t A = smem_u32(ring + s * st_bytes), B = A + a_bytes;
+            for (int kk = 0; kk < cin / 16; ++kk) {
+                const uint64_t ad = umma_desc(A + kk * (kTcRows * 32), 128, 256);
+                const uint64_t bd = umma_desc(B + kk * (COUT * 32), 128, 256);
+                const uint32_t acc = (t | kk) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc) : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                         ::"r"(bar0 + 8 * s) : "memory");
+        }
+        // refill the buffer of tap t - 1 with tap t + 2 once its MMAs have completed
+        const int nt = t + kTcStages - 1;
+        if (nt < 27) {
+            const int s = nt % kTcStages;
+            if (nt >= kTcStages) ok &= mbar_wait(bar0 + 8 * s, (uint32_t)((nt / kTcStages - 1) & 1));
+            stage(nt, s);
+        }
+        cp_async_commit();
+    }
+    // the last commit (tap 26) covers every MMA of this CTA
+    ok &= mbar_wait(bar0 + 8 * (26 % kTcStages), (uint32_t)((26 / kTcStages) & 1));
+    ok = __syncthreads_and(ok);                // the warp-collective reads below need one answer
+    tc_fence_after();
+    if (ok) {
+        float acc[COUT];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-            for (int j = 0; j < COUT / 8; ++j) {
-                const bf16 *wr = Wtap + (size_t)(j * 8 + g) * cin + c0 + 2 * t;
-                const unsigned b0 = __ldg(reinterpret_cast<const unsigned *>(wr));
-                const unsigned b1 = __ldg(reinterpret_cast<const unsigned *>(wr + 8));
-                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
+        for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, acc + c0);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (valid) {
+            bf16 *yr = Y + p * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; c += 8) {
+                float o[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    o[i] = acc[c + i] + (bias ? bias[c + i] : 0.f);
+                    if (relu) o[i] = fmaxf(o[i], 0.f);
+                }
+                uint4 pk;
+                pk.x = pack_bf16(o[0], o[1]);
+                pk.y = pack_bf16(o[2], o[3]);
+                pk.z = pack_bf16(o[4], o[5]);
+                pk.w = pack_bf16(o[6], o[7]);
+                *reinterpret_cast<uint4 *>(yr + c) = pk;
             }
         }
+    } else if (tid == 0) {
+        atomicOr(err, 1u);
     }
-    // epilogue: bias, ReLU, BF16, channels-innermost store
-    bf16 *Ya = Y + (p0 + g) * COUT, *Yb = Y + (p0 + g + 8) * COUT;
-#pragma unroll
-    for (int j = 0; j < COUT / 8; ++j) {
-        const int co = j * 8 + 2 * t;
-        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-        float v0 = acc[j][0] + b0, v1 = acc[j][1] + b1, v2 = acc[j][2] + b0, v3 = acc[j][3] + b1;
-        if (relu) {
-            v0 = fmaxf(v0, 0.f); v1 = fmaxf(v1, 0.f); v2 = fmaxf(v2, 0.f); v3 = fmaxf(v3, 0.f);
-        }
-        *reinterpret_cast<unsigned *>(Ya + co) = pack_bf16(v0, v1);
-        *reinterpret_cast<unsigned *>(Yb + co) = pack_bf16(v2, v3);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
     }
 }
 
@@ -429,19 +585,30 @@ unsigned grid1(long long n)
     return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32));
 }
 
-cudaError_t launch_fwd(const bf16 *X, int cin, const bf16 *W, const float *bias, Vol v, int cout,
-                       int relu, bf16 *Y, cudaStream_t st)
+template <int COUT>
+cudaError_t launch_tc_t(const bf16 *X, int cin, const bf16 *W, const float *bias, Vol v, int relu,
+                        bf16 *Y, unsigned *err, cudaStream_t st)
 {
-    const unsigned blocks = (unsigned)((v.pos() / 16 + 3) / 4);
+    const int smem = tc_smem_bytes(cin, COUT);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((v.pos() + kTcRows - 1) / kTcRows);
+    conv3d_fwd_tc<COUT><<<blocks, 128, smem, st>>>(X, cin, W, bias, v, relu, Y, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_tc(const bf16 *X, int cin, const bf16 *W, const float *bias, Vol v, int cout,
+                          int relu, bf16 *Y, unsigned *err, cudaStream_t st)
+{
+    if (cin % 16 || cin < 16 || cin > 96) return cudaErrorInvalidValue;
     switch (cout) {
-    case 16: conv3d_fwd<16><<<blocks, 128, 0, st>>>(X, cin, W, bias, v, relu, Y); break;
-    case 32: conv3d_fwd<32><<<blocks, 128, 0, st>>>(X, cin, W, bias, v, relu, Y); break;
-    case 48: conv3d_fwd<48><<<blocks, 128, 0, st>>>(X, cin, W, bias, v, relu, Y); break;
-    case 64: conv3d_fwd<64><<<blocks, 128, 0, st>>>(X, cin, W, bias, v, relu, Y); break;
-    case 96: conv3d_fwd<96><<<blocks, 128, 0, st>>>(X, cin, W, bias, v, relu, Y); break;
+    case 16: return launch_tc_t<16>(X, cin, W, bias, v, relu, Y, err, st);
+    case 32: return launch_tc_t<32>(X, cin, W, bias, v, relu, Y, err, st);
+    case 48: return launch_tc_t<48>(X, cin, W, bias, v, relu, Y, err, st);
+    case 64: return launch_tc_t<64>(X, cin, W, bias, v, relu, Y, err, st);
+    case 96: return launch_tc_t<96>(X, cin, W, bias, v, relu, Y, err, st);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_w(const bf16 *X, int cin, const bf16 *dY, int cout, Vol v, float *dW,
@@ -494,6 +661,7 @@ struct mcx_denoiser {
     DBuf x16, a[10], p1, p2, u2, u1, out, loss;
     DBuf g_x16, ga[10], gp1, gp2, gu2, gu1, gtmp;
     DBuf xin;                           // encoded input of apply()
+    DBuf status;                        // set when a tensor-core wait timed out
     float floor_ = 1e-8f, mu = -4.f, sigma = 2.f;
     long long step = 0;
     std::string err;
@@ -513,6 +681,18 @@ static mcx_status dn_fail(mcx_denoiser *d, mcx_status st, const std::string &m)
             return dn_fail((d), e_ == cudaErrorMemoryAllocation ? MCX_E_OOM : MCX_E_CUDA,      \
                            std::string(what) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
+
+// after the device has been synchronised: reports (and clears) a tensor-core wait timeout
+static mcx_status check_status(mcx_denoiser *d)
+{
+    unsigned h = 0;
+    DNC(d, cudaMemcpy(&h, d->status.p, 4, cudaMemcpyDeviceToHost), "reading the status");
+    if (h) {
+        DNC(d, cudaMemset(d->status.p, 0, 4), "clearing the status");
+        return dn_fail(d, MCX_E_TIMEOUT, "a tensor-core pipeline wait timed out; results are invalid");
+    }
+    return MCX_OK;
+}
 
 static Vol level_vol(const mcx_denoiser *d, int level, int n)
 {
@@ -537,8 +717,8 @@ static mcx_status forward(mcx_denoiser *d, const float *x, int n, float *out, cu
     const float *P = d->params.as<float>();
     pad_input<<<grid1(v0.pos() * 16), 256, 0, st>>>(x, v0.pos(), d->x16.as<bf16>());
     auto conv = [&](int l, const bf16 *in, Vol v) {
-        return launch_fwd(in, kLayers[l].cin, d->wf[l].as<bf16>(), P + d->b_off[l], v,
-                          kLayers[l].cout, 1, d->a[l].as<bf16>(), st);
+        return launch_fwd_tc(in, kLayers[l].cin, d->wf[l].as<bf16>(), P + d->b_off[l], v,
+                             kLayers[l].cout, 1, d->a[l].as<bf16>(), d->status.as<unsigned>(), st);
     };
     DNC(d, conv(0, d->x16.as<bf16>(), v0), "conv e1a");
     DNC(d, conv(1, d->a[0].as<bf16>(), v0), "conv e1b");
@@ -570,7 +750,9 @@ static mcx_status conv_bwd(mcx_denoiser *d, int l, const bf16 *in, Vol v, bf16 *
     relu_mask<<<grid1(v.pos() * L.cout), 256, 0, st>>>(dA, d->a[l].as<bf16>(), v.pos() * L.cout);
     bias_grad<<<dim3(64, L.cout), 256, 0, st>>>(dA, v.pos(), L.cout, G + d->b_off[l]);
     DNC(d, launch_bwd_w(in, L.cin, dA, L.cout, v, G + d->w_off[l], st), "weight gradient");
-    if (dIn) DNC(d, launch_fwd(dA, L.cout, d->wb[l].as<bf16>(), nullptr, v, L.cin, 0, dIn, st), "input gradient");
+    if (dIn)
+        DNC(d, launch_fwd_tc(dA, L.cout, d->wb[l].as<bf16>(), nullptr, v, L.cin, 0, dIn, d->status.as<unsigned>(), st),
+            "input gradient");
     return MCX_OK;
 }
 
@@ -657,8 +839,10 @@ mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uin
     A(d->x16, p0 * 16 * B2); A(d->p1, p1 * 16 * B2); A(d->p2, p2 * 32 * B2);
     A(d->u2, p1 * 96 * B2); A(d->u1, p0 * 48 * B2); A(d->out, p0 * 4); A(d->loss, 4);
     A(d->xin, p0 * 4);
+    A(d->status, 4);
     A(d->gp1, p1 * 16 * B2); A(d->gp2, p2 * 32 * B2); A(d->gu2, p1 * 96 * B2); A(d->gu1, p0 * 48 * B2);
     if (e == cudaSuccess) e = cudaMemcpy(d->params.p, init.data(), d->nparam * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d->status.p, 0, 4);
     if (e == cudaSuccess) e = cudaMemset(d->m1.p, 0, d->nparam * 4);
     if (e == cudaSuccess) e = cudaMemset(d->m2.p, 0, d->nparam * 4);
     if (e != cudaSuccess) {
@@ -685,6 +869,7 @@ mcx_status mcx_denoiser_get_params(mcx_denoiser *d, float *host, uint64_t n, int
     if (!d || !host) return dn_fail(d, MCX_E_ARG, "NULL argument");
     if (n != d->nparam) return dn_fail(d, MCX_E_ARG, "n must equal the parameter count");
     DNC(d, cudaDeviceSynchronize(), "waiting");
+    if (mcx_status s = check_status(d)) return s;
     const DBuf &src = which == 1 ? d->grads : d->params;
     DNC(d, cudaMemcpy(host, src.p, n * 4, cudaMemcpyDeviceToHost), "reading parameters");
     return MCX_OK;
@@ -740,6 +925,7 @@ mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const fl
     if (loss_host) {
         DNC(d, cudaMemcpyAsync(loss_host, d->loss.p, 4, cudaMemcpyDeviceToHost, st), "reading the loss");
         DNC(d, cudaStreamSynchronize(st), "waiting for the step");
+        return check_status(d);
     }
     return MCX_OK;
 }
@@ -810,6 +996,13 @@ mcx_status mcx_denoiser_gather(mcx_denoiser *d, const float *set_dev, uint64_t s
     return MCX_OK;
 }
 
+mcx_status mcx_denoiser_sync(mcx_denoiser *d)
+{
+    if (!d) return dn_fail(nullptr, MCX_E_ARG, "NULL denoiser");
+    DNC(d, cudaDeviceSynchronize(), "waiting");
+    return check_status(d);
+}
+
 void mcx_denoiser_destroy(mcx_denoiser *d)
 {
     if (!d) return;
@@ -824,7 +1017,7 @@ mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t dd, int32_t hh, int
                             int32_t cout, const float *x, const float *w, const float *bias,
                             const float *dy, float *out)
 {
-    if (!x || !out || (kind == 0 && !w) || (kind == 1 && !dy) || ww % 16 || n < 1)
+    if (!x || !out || kind < 0 || kind > 1 || (kind == 0 && !w) || (kind == 1 && !dy) || ww % 16 || n < 1)
         return dn_fail(nullptr, MCX_E_ARG, "bad arguments");
     const Vol v{n, dd, hh, ww};
     const long long P = v.pos();
@@ -841,7 +1034,15 @@ mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t dd, int32_t hh, int
         if (e == cudaSuccess && bias) e = bb.alloc(cout * 4);
         if (e == cudaSuccess && bias) e = cudaMemcpy(bb.p, bias, cout * 4, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = by.alloc(P * cout * 2);
-        if (e == cudaSuccess) e = launch_fwd(bx.as<bf16>(), cin, bw.as<bf16>(), bias ? bb.as<float>() : nullptr, v, cout, 1, by.as<bf16>(), nullptr);
+        DBuf berr;
+        if (e == cudaSuccess) e = berr.alloc(4);
+        if (e == cudaSuccess) e = cudaMemset(berr.p, 0, 4);
+        if (e == cudaSuccess)
+            e = launch_fwd_tc(bx.as<bf16>(), cin, bw.as<bf16>(), bias ? bb.as<float>() : nullptr, v, cout, 1,
+                              by.as<bf16>(), berr.as<unsigned>(), nullptr);
+        unsigned herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, berr.p, 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && herr) return dn_fail(nullptr, MCX_E_TIMEOUT, "tensor-core wait timed out");
         std::vector<bf16> hy(P * cout);
         if (e == cudaSuccess) e = cudaMemcpy(hy.data(), by.p, hy.size() * 2, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) for (size_t i = 0; i < hy.size(); ++i) out[i] = __bfloat162float(hy[i]);

@@ -116,6 +116,7 @@ def test_network_forward_matches_oracle(g, torch_cuda):
         xd = torch.tensor(x, device="cuda")
         yd = torch.empty_like(xd)
         d.forward(xd, yd)
+        d.sync()
         y = yd.cpu().numpy().astype(np.float64)
     ref = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=True).numpy()
     exact = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=False).numpy()
@@ -194,7 +195,7 @@ def test_apply_is_encode_forward_decode(g, torch_cuda):
         xe = x.cpu().numpy()
         assert np.allclose(xe, od.encode(phi), rtol=0, atol=2e-6)
         d.decode(x, back)
-        torch.cuda.synchronize()
+        d.sync()
         dec = back.cpu().numpy()
         assert np.allclose(dec, od.decode(xe.astype(np.float64)), rtol=2e-5, atol=1e-12)
 
