@@ -337,7 +337,8 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
    phi = max(10^(x sigma + mu) - floor, 0); defaults floor 1e-8, mu -4, sigma 2.
 
    Volumes are FP32 [n][nz][ny][nx] device arrays on the denoiser's device, n <= max_batch.
-   Sizes: nx a multiple of 64, ny and nz multiples of 4.  The object owns every buffer it
+   Sizes: nx a multiple of 64 up to 252 (so nx = 64 or 128), ny and nz multiples of 4,
+   max_batch * nx * ny * nz * 96 < 2^31.  The object owns every buffer it
    needs (activations for max_batch volumes); calls on one object must not overlap.
    Errors: MCX_E_ARG (bad sizes or NULL), MCX_E_OOM, MCX_E_CUDA, MCX_E_TIMEOUT (see
    mcx_denoiser_sync), described by mcx_last_error(NULL). */
@@ -400,12 +401,13 @@ mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
 
 /* One 3x3x3 convolution of the denoiser on host arrays, run by the denoiser's own
    tensor-core kernels (tcgen05 for kind 0, warp-level mma for kind 1); values are rounded
-   to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16:
+   to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16 up to 254:
      kind 0: forward,  x [n][nz][ny][nx][cin], w [27][cout][cin], bias [cout] or NULL
              -> out = ReLU(conv + bias) [n][nz][ny][nx][cout], rounded to BF16
      kind 1: weight gradient, x as above, dy [n][nz][ny][nx][cout]
              -> out [27][cout][cin] = sum over positions of dy * x(shifted by the tap), FP32
-   cin and cout from {16, 32, 48, 64, 96}. */
+   (cin, cout) one of the network's pairs: (16,16) (16,32) (16,48) (32,16) (32,32) (32,64)
+   (32,96) (48,16) (64,32) (64,64) (96,32). */
 mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t nz, int32_t ny, int32_t nx,
                             int32_t cin, int32_t cout, const float *x, const float *w,
                             const float *bias, const float *dy, float *out);

@@ -23,6 +23,8 @@
 //   head: 1x1x1 conv 16->1 (FP32), added to the input
 // Every 3x3x3 convolution has a bias and ReLU; the input layer sees the single input
 // channel padded to 16 with zeros.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -63,55 +65,40 @@ struct Vol {
 
 // ------------------------------------------------------------------------ convolution
 // Y[p][co] = act(bias[co] + sum_tap sum_ci X[p + off(tap)][ci] * W[tap][co][ci]) (zero
-// outside the volume) as an implicit GEMM on the 5th-generation tensor cores: one CTA
-// (4 warps) computes 128 consecutive output positions x COUT channels as
-// D[128][COUT] += A_tap[128][cin] * W_tap[cin][COUT] over the 27 taps, with D in tensor
-// memory (FP32, one TMEM lane per position).  Each tap's operands are staged into shared memory by cp.async (zero-filled
-// where the tap reads outside the volume) through a 3-buffer ring; one thread issues the
-// tcgen05.mma instructions (K = 16 each) and tcgen05.commit signals an mbarrier when a
-// buffer may be refilled.  Operand layout (K-major, no swizzle, 16-byte core-matrix rows):
-// for each 16-channel slice kk, 8-row groups of two 8-channel core matrices:
-//   byte(row r, 8-channel chunk c) = (c / 2) * (rows * 32) + (r / 8) * 256 + (c % 2) * 128 + (r % 8) * 16
-// so an instruction's operand starts at slice kk with leading-dimension (K) offset 128 B and
-// stride-dimension (M/N) offset 256 B.  Every wait is bounded: on a timeout the CTA records
-// an error, still waits (bounded) for its own MMAs, frees its tensor memory and returns.
+// outside the volume) as an implicit GEMM on the 5th-generation tensor cores.
+//
+// Tiles.  Within one z-plane, positions are numbered along padded lines of pitch
+// PW = W + 2: q = y * PW + (x + 1), so x = -1 and x = W are pad columns.  A tile is 128
+// consecutive q (GEMM rows M = 128); rows that land on pad columns or past the last line
+// are computed and discarded.  In this numbering the tap (dz, dy, dx) reads row
+// q + dy * PW + dx of plane z + dz, so for a fixed dz all nine (dy, dx) taps read one
+// window of consecutive rows at offsets dy * PW + dx.  The window is one TMA box of
+// [8 channels][PW columns from x = -1][L lines][1 plane][1 volume] per 8-channel chunk:
+// the tensor map's out-of-bounds fill supplies the zero padding (x = -1, x = W, lines and
+// planes outside the volume), and the box lands in shared memory as consecutive 16-byte
+// rows in q order -- already the K-major no-swizzle operand layout (8-row core matrices
+// 128 B apart; chunks one leading-dimension offset apart), so a one-row shift of the
+// operand is a 16-byte shift of its start address.  A tile takes 3 windows (one per
+// plane); each feeds 9 taps x cin/16 tcgen05.mma instructions (K = 16, N = COUT).
+//
+// Warp roles (6 warps, persistent over tiles): warp 0 lane 0 issues the TMA loads into a
+// ring of stages (mbarrier "full" with transaction bytes); warp 1 lane 0 issues the MMAs
+// and commits to "empty" (the stage may be refilled) and, after a tile's last window, to
+// "acc full"; warps 2-5 read the accumulator out (tcgen05.ld; warp w reads TMEM lanes
+// 32 (w mod 4) ...), arrive on "acc empty", and store bias + ReLU in BF16 for the valid
+// rows.  Two TMEM accumulators let a tile's read-out overlap the next tile's MMAs.  The
+// layer's weights stay resident in shared memory when they fit (one TMA load each), else
+// each stage also carries its plane's 9 taps of weights.
+//
+// Every wait is bounded: on a timeout the role records an error and stops; the CTA still
+// waits (bounded) for its TMA loads and frees its tensor memory.
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-template <int N> __device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (int it = 0; it < (1 << 22); ++it) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
 
 // shared-memory matrix descriptor: start, leading- and stride-dimension byte offsets,
 // descriptor version 1 (bits 46-47), no swizzle
@@ -141,142 +128,261 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int kTcRows = 128, kTcStages = 3, kTcHeader = 128, kTcSlack = 8192;
+constexpr int kTcRows = 128, kTcThreads = 192, kTcHeader = 256;
+constexpr int kTcWallMax = 64 * 1024;       // weights up to this size stay resident
+constexpr int kTcSmemBudget = 112 * 1024;   // preferred shared memory per CTA
+constexpr int kTcSmemMax = 227 * 1024;      // shared memory one CTA may use
+constexpr int kTcMaxStages = 8;
 
-__host__ __device__ constexpr int tc_stage_bytes(int cin, int cout) { return (kTcRows + cout) * cin * 2; }
-
-__host__ __device__ constexpr int tc_smem_bytes(int cin, int cout)
+__host__ __device__ constexpr bool tc_wall(int cin, int cout) { return 27 * cin * cout * 2 <= kTcWallMax; }
+// lines of a window: the tile's rows q0 - 1 - PW .. q0 + 128 + PW
+__host__ __device__ constexpr int tc_lines(int w) { return (kTcRows + 2 + w + 1) / (w + 2) + 3; }
+// one 8-channel chunk of a window: L lines x PW rows of 16 B, padded to 128 B
+__host__ __device__ constexpr int tc_lbo_a(int w) { return ((tc_lines(w) * (w + 2) * 16 + 127) / 128) * 128; }
+__host__ __device__ constexpr int tc_stage_bytes(int cin, int cout, int w)
 {
-    return kTcHeader + kTcStages * tc_stage_bytes(cin, cout) + kTcSlack;
+    return (cin / 8) * tc_lbo_a(w) + (tc_wall(cin, cout) ? 0 : 9 * cout * cin * 2);
+}
+__host__ __device__ constexpr int tc_smem_bytes(int cin, int cout, int w, int ns)
+{
+    return 1024 + kTcHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + ns * tc_stage_bytes(cin, cout, w);
+}
+// ring depth: 4-8 stages within kTcSmemBudget (two or more CTAs per SM), else 2-4 stages
+// within one SM's shared memory; 0 when not even 2 fit
+__host__ __device__ constexpr int tc_stages(int cin, int cout, int w)
+{
+    for (int ns = kTcMaxStages; ns >= 4; --ns)
+        if (tc_smem_bytes(cin, cout, w, ns) <= kTcSmemBudget) return ns;
+    for (int ns = 4; ns >= 2; --ns)
+        if (tc_smem_bytes(cin, cout, w, ns) <= kTcSmemMax) return ns;
+    return 0;
 }
 
-template <int COUT>
-__global__ void __launch_bounds__(128)
-conv3d_fwd_tc(const bf16 *__restrict__ X, int cin, const bf16 *__restrict__ Wt,
-              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns
-    constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t bar0 = smem_u32(smem);                     // 3 mbarriers, 8 B each
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 64);
-    unsigned char *ring = smem + kTcHeader;
-    const int a_bytes = kTcRows * cin * 2, st_bytes = tc_stage_bytes(cin, COUT);
-    const int tid = threadIdx.x, warp = tid >> 5;
-
-    const long long P = v.pos();
-    const long long p = (long long)blockIdx.x * kTcRows + tid;  // this thread's row
-    const bool valid = p < P;
-    int x = 0, y = 0, z = 0, b = 0;
-    if (valid) {
-        long long r = p;
-        x = (int)(r % v.w); r /= v.w;
-        y = (int)(r % v.h); r /= v.h;
-        z = (int)(r % v.d);
-        b = (int)(r / v.d);
+    for (int it = 0; it < (1 << 22); ++it) {       // about a second of polling at most
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
     }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+                   "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];\n"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar) : "memory");
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kTcThreads)
+conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err, int ns)
+{
+    constexpr int cin = CIN;
+    constexpr bool WALL = tc_wall(CIN, COUT);
+    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns per accumulator
+    constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
+    // header: full[ns] at 0, empty[ns] at 64, acc full[2] at 128, acc empty[2] at 144,
+    // weights barrier at 160, TMEM address at 192
+    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 144, wbar = base + 160;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 192 - smem_u32(smem_raw)));
+    const int wtap = COUT * cin * 2, lbo_b = COUT * 16;
+    const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
+    const int a_bytes = (cin / 8) * lbo_a;
+    const uint32_t wres = base + kTcHeader;
+    const uint32_t ring = wres + (WALL ? 27 * wtap : 0);
+    const int stage_bytes = a_bytes + (WALL ? 0 : 9 * wtap);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
+    const int n_tiles = v.n * v.d * tiles_plane;
+    const int my_tiles = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_steps = my_tiles * 3;
+
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     ::"r"(smem_u32(tslot)), "r"(NCOL) : "memory");
+                     ::"r"(smem_u32(tslot)), "r"(2 * NCOL) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8 * s) : "memory");
+        for (int b = 0; b < ns; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4 * 32);
+        }
+        mbar_init(wbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    // stage tap `tap` into ring buffer s
-    auto stage = [&](int tap, int s) {
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const uint32_t A = smem_u32(ring + s * st_bytes), B = A + a_bytes;
-        const int xs = x + dx, ys = y + dy, zs = z + dz;
-        const bool in = valid && xs >= 0 && xs < v.w && ys >= 0 && ys < v.h && zs >= 0 && zs < v.d;
-        const bf16 *src = in ? X + ((((long long)b * v.d + zs) * v.h + ys) * v.w + xs) * cin : X;
-        const uint32_t arow = A + (tid >> 3) * 256 + (tid & 7) * 16;
-        for (int c = 0; c < cin / 8; ++c)
-            cp_async16(arow + (c >> 1) * (kTcRows * 32) + (c & 1) * 128, src + (in ? 8 * c : 0), in ? 16u : 0u);
-        const bf16 *wt = Wt + (size_t)tap * COUT * cin;
-        for (int i = tid; i < COUT * (cin / 8); i += 128) {
-            const int co = i % COUT, c = i / COUT;
-            cp_async16(B + (c >> 1) * (COUT * 32) + (co >> 3) * 256 + (c & 1) * 128 + (co & 7) * 16,
-                       wt + (size_t)co * cin + 8 * c, 16u);
-        }
-    };
-
     bool ok = true;
-    stage(0, 0);
-    cp_async_commit();
-    stage(1, 1);
-    cp_async_commit();
-    for (int t = 0; t < 27; ++t) {
-        cp_async_wait<1>();                    // this thread's copies of tap t have landed
-        fence_proxy_async_smem();              // make them visible to the tensor cores
-        __syncthreads();
-        if (tid == 0) {
+
+    auto tile_q0 = [&](int t, int &b, int &z) {              // local tile t -> (volume, plane, q0)
+        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+        const int plane = tile / tiles_plane;
+        z = plane % v.d;
+        b = plane / v.d;
+        return (tile % tiles_plane) * kTcRows;
+    };
+    // first window line: one above the line of q0 - 1
+    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
+
+    if (tid == 0) {
+        // ------------------------------------------------------------ producer (TMA)
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
+        if (WALL && n_steps) {
+            mbar_expect_tx(wbar, 27 * wtap);
+            for (int tap = 0; tap < 27; ++tap)
+                for (int c = 0; c < cin / 8; ++c)
+                    tma_load_2d(wres + tap * wtap + c * lbo_b, &tmw, 8 * c, tap * COUT, wbar);
+        }
+        const uint32_t tx = a_bytes / lbo_a * (L * PW * 16) + (WALL ? 0 : 9 * wtap);
+        int b = 0, use = 0;
+        for (int s = 0; s < n_steps && ok; ++s) {
+            if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
+            if (!ok) break;
+            int vb, z;
+            const int q0 = tile_q0(s / 3, vb, z);
+            const int g = s % 3;                               // plane z + g - 1
+            const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
+            mbar_expect_tx(fb, tx);
+            for (int c = 0; c < cin / 8; ++c)
+                tma_load_5d(st + c * lbo_a, &tmx, 8 * c, -1, first_line(q0), z + g - 1, vb, fb);
+            if (!WALL)
+                for (int tt = 0; tt < 9; ++tt)
+                    for (int c = 0; c < cin / 8; ++c)
+                        tma_load_2d(st + a_bytes + tt * wtap + c * lbo_b, &tmw, 8 * c, (9 * g + tt) * COUT, fb);
+            if (++b == ns) { b = 0; ++use; }
+        }
+        // every load issued has landed before the CTA may exit
+        for (int bb = 0; bb < ns; ++bb) {
+            const int issued = use + (bb < b ? 1 : 0);       // fills of buffer bb
+            if (issued > 0) ok &= mbar_wait(full0 + 8 * bb, (uint32_t)((issued - 1) & 1));
+        }
+        if (WALL && n_steps) ok &= mbar_wait(wbar, 0);
+    } else if (tid == 32) {
+        // ------------------------------------------------------------ MMA issuer
+        if (WALL && n_steps) ok &= mbar_wait(wbar, 0);
+        const uint64_t adesc0 = umma_desc(ring, lbo_a, 128);
+        const uint64_t bdesc0 = umma_desc(WALL ? wres : ring + a_bytes, lbo_b, 128);
+        int toff[9];                                            // row offset of each (dy, dx) tap
+#pragma unroll
+        for (int tt = 0; tt < 9; ++tt) toff[tt] = (tt / 3 - 1) * PW + (tt % 3 - 1);
+        int b = 0, use = 0;
+        for (int s = 0; s < n_steps && ok; ++s) {
+            const int t = s / 3, g = s % 3, acc = t & 1;
+            if (g == 0 && t >= 2) ok &= mbar_wait(acce0 + 8 * acc, (uint32_t)(((t >> 1) - 1) & 1));
+            ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
+            if (!ok) break;
             tc_fence_after();
-            const int s = t % kTcStages;
-            const uint32_t A = smem_u32(ring + s * st_bytes), B = A + a_bytes;
-            for (int kk = 0; kk < cin / 16; ++kk) {
-                const uint64_t ad = umma_desc(A + kk * (kTcRows * 32), 128, 256);
-                const uint64_t bd = umma_desc(B + kk * (COUT * 32), 128, 256);
-                const uint32_t acc = (t | kk) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc) : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                         ::"r"(bar0 + 8 * s) : "memory");
-        }
-        // refill the buffer of tap t - 1 with tap t + 2 once its MMAs have completed
-        const int nt = t + kTcStages - 1;
-        if (nt < 27) {
-            const int s = nt % kTcStages;
-            if (nt >= kTcStages) ok &= mbar_wait(bar0 + 8 * s, (uint32_t)((nt / kTcStages - 1) & 1));
-            stage(nt, s);
-        }
-        cp_async_commit();
-    }
-    // the last commit (tap 26) covers every MMA of this CTA
-    ok &= mbar_wait(bar0 + 8 * (26 % kTcStages), (uint32_t)((26 / kTcStages) & 1));
-    ok = __syncthreads_and(ok);                // the warp-collective reads below need one answer
-    tc_fence_after();
-    if (ok) {
-        float acc[COUT];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            int vb, z;
+            const int q0 = tile_q0(t, vb, z);
+            const int off = q0 - first_line(q0) * PW;           // window row of q0
+            // descriptors differ only in the start-address field (address / 16, 14 bits;
+            // every address here is below 256 KiB), so each instruction's pair is the
+            // stage's base descriptor plus a constant offset
+            const uint64_t abase = adesc0 + (uint64_t)((b * stage_bytes + off * 16) >> 4);
+            const uint64_t bbase = bdesc0 + (uint64_t)((WALL ? 9 * g * wtap : b * stage_bytes) >> 4);
+            const uint32_t d = tmem + acc * NCOL;
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, acc + c0);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (valid) {
-            bf16 *yr = Y + p * COUT;
+            for (int tt = 0; tt < 9; ++tt)                      // tt = 3 (dy + 1) + (dx + 1)
 #pragma unroll
-            for (int c = 0; c < COUT; c += 8) {
-                float o[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    o[i] = acc[c + i] + (bias ? bias[c + i] : 0.f);
-                    if (relu) o[i] = fmaxf(o[i], 0.f);
+                for (int kk = 0; kk < CIN / 16; ++kk) {
+                    const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                    const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
+                    const uint32_t accum = (g | tt | kk) ? 1u : 0u;
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
                 }
-                uint4 pk;
-                pk.x = pack_bf16(o[0], o[1]);
-                pk.y = pack_bf16(o[2], o[3]);
-                pk.z = pack_bf16(o[4], o[5]);
-                pk.w = pack_bf16(o[6], o[7]);
-                *reinterpret_cast<uint4 *>(yr + c) = pk;
+            tc_commit(empty0 + 8 * b);
+            if (g == 2) tc_commit(accf0 + 8 * acc);
+            if (++b == ns) { b = 0; ++use; }
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
+        for (int t = 0; t < my_tiles && ok; ++t) {
+            const int acc = t & 1;
+            ok &= mbar_wait(accf0 + 8 * acc, (uint32_t)((t >> 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);                   // the collective reads below
+            if (!ok) break;
+            tc_fence_after();
+            float a[COUT];
+            const uint32_t taddr = tmem + acc * NCOL + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+            for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, a + c0);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(acce0 + 8 * acc);
+            int vb, z;
+            const int q = tile_q0(t, vb, z) + r, y = q / PW, x = q - y * PW - 1;
+            if (y < v.h && x >= 0 && x < v.w) {
+                bf16 *yr = Y + ((((long long)vb * v.d + z) * v.h + y) * v.w + x) * COUT;
+#pragma unroll
+                for (int c = 0; c < COUT; c += 8) {
+                    float o[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        o[i] = a[c + i] + (bias ? __ldg(bias + c + i) : 0.f);
+                        if (relu) o[i] = fmaxf(o[i], 0.f);
+                    }
+                    uint4 pk;
+                    pk.x = pack_bf16(o[0], o[1]);
+                    pk.y = pack_bf16(o[2], o[3]);
+                    pk.z = pack_bf16(o[4], o[5]);
+                    pk.w = pack_bf16(o[6], o[7]);
+                    *reinterpret_cast<uint4 *>(yr + c) = pk;
+                }
             }
         }
-    } else if (tid == 0) {
-        atomicOr(err, 1u);
     }
+    if (!__syncthreads_and(ok) && tid == 0) atomicOr(err, 1u);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * NCOL) : "memory");
     }
 }
 
@@ -348,156 +454,223 @@ conv3d_bwd_w(const bf16 *__restrict__ X, const bf16 *__restrict__ dY, int cout, 
 }
 
 // ------------------------------------------------------------------------ elementwise
-__global__ void relu_mask(bf16 *dY, const bf16 *Y, long long n)
+// Elementwise layer kernels on 8-channel (16-byte) chunks; every count and index fits in
+// 32 bits (mcx_denoiser_create bounds max_batch * nx * ny * nz * 96).
+struct Bf8 {
+    uint4 u;
+    __device__ void to(float *f) const
+    {
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 t = __bfloat1622float2(h[i]);
+            f[2 * i] = t.x;
+            f[2 * i + 1] = t.y;
+        }
+    }
+    __device__ static Bf8 from(const float *f)
+    {
+        Bf8 r;
+        r.u.x = pack_bf16(f[0], f[1]);
+        r.u.y = pack_bf16(f[2], f[3]);
+        r.u.z = pack_bf16(f[4], f[5]);
+        r.u.w = pack_bf16(f[6], f[7]);
+        return r;
+    }
+};
+
+__device__ __forceinline__ uint4 ld16(const bf16 *p) { return *reinterpret_cast<const uint4 *>(p); }
+__device__ __forceinline__ void st16(bf16 *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+
+// position p of volume v -> its coarse parent (v's dimensions halved)
+__device__ __forceinline__ int parent_of(int p, const Vol &v)
 {
-    const long long s = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += s)
-        if (__bfloat162float(Y[i]) <= 0.f) dY[i] = __float2bfloat16(0.f);
+    const int x = p % v.w;
+    int r = p / v.w;
+    const int y = r % v.h;
+    r /= v.h;
+    const int z = r % v.d, b = r / v.d;
+    return ((b * (v.d >> 1) + (z >> 1)) * (v.h >> 1) + (y >> 1)) * (v.w >> 1) + (x >> 1);
 }
 
-__global__ void bias_grad(const bf16 *dY, long long npos, int c, float *db)
+// the 8 children of coarse position pc (fine volume vf) as fine indices
+__device__ __forceinline__ void children_of(int pc, const Vol &vf, int *ch)
 {
-    // one thread per (channel, slice of positions)
+    const int wc = vf.w >> 1, hc = vf.h >> 1, dc = vf.d >> 1;
+    const int x = pc % wc;
+    int r = pc / wc;
+    const int y = r % hc;
+    r /= hc;
+    const int z = r % dc, b = r / dc;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        ch[k] = ((b * vf.d + 2 * z + (k >> 2)) * vf.h + 2 * y + ((k >> 1) & 1)) * vf.w + 2 * x + (k & 1);
+}
+
+#define GRID_LOOP(i, n) \
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// ReLU backward: zero the gradient where the stored output is not positive
+__global__ void relu_mask(bf16 *dY, const bf16 *Y, int n8)
+{
+    GRID_LOOP(i, n8) {
+        float y[8], g[8];
+        Bf8{ld16(Y + 8 * i)}.to(y);
+        Bf8{ld16(dY + 8 * i)}.to(g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (y[k] <= 0.f) g[k] = 0.f;
+        st16(dY + 8 * i, Bf8::from(g).u);
+    }
+}
+
+__global__ void bias_grad(const bf16 *dY, int npos, int c, float *db)
+{
+    // one block column per channel, a slice of positions per thread
     const int ch = blockIdx.y;
     float s = 0.f;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npos; p += stride)
-        s += __bfloat162float(dY[p * c + ch]);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += gridDim.x * blockDim.x)
+        s += __bfloat162float(dY[(size_t)p * c + ch]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(db + ch, s);
 }
 
 // input layer: the FP32 input as channel 0 of a 16-channel BF16 volume
-__global__ void pad_input(const float *x, long long npos, bf16 *X16)
+__global__ void pad_input(const float *x, int npos, bf16 *X16)
 {
-    const long long s = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npos * 16; i += s)
-        X16[i] = __float2bfloat16((i & 15) == 0 ? x[i >> 4] : 0.f);
+    GRID_LOOP(p, npos) {
+        float f[8] = {x[p], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        st16(X16 + 16 * p, Bf8::from(f).u);
+        st16(X16 + 16 * p + 8, make_uint4(0u, 0u, 0u, 0u));
+    }
 }
 
-__global__ void avgpool_fwd(const bf16 *X, Vol vo, int c, bf16 *Y)   // vo: output volume
+// 2x2x2 average pooling; vo is the output (coarse) volume
+__global__ void avgpool_fwd(const bf16 *X, Vol vo, int c, bf16 *Y)
 {
-    const long long n = vo.pos() * c, s = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += s) {
-        const int ch = (int)(i % c);
-        long long p = i / c;
-        const int x = (int)(p % vo.w); p /= vo.w;
-        const int y = (int)(p % vo.h); p /= vo.h;
-        const int z = (int)(p % vo.d);
-        const int b = (int)(p / vo.d);
-        const int W = 2 * vo.w, H = 2 * vo.h, D = 2 * vo.d;
-        float acc = 0.f;
+    const int c8 = c / 8, n = vo.n * vo.d * vo.h * vo.w * c8;
+    const Vol vf{vo.n, 2 * vo.d, 2 * vo.h, 2 * vo.w};
+    GRID_LOOP(i, n) {
+        const int pc = i / c8, j = i - pc * c8;
+        int ch[8];
+        children_of(pc, vf, ch);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const long long q = (((long long)b * D + 2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W + 2 * x + (k & 1);
-            acc += __bfloat162float(X[q * c + ch]);
+            float f[8];
+            Bf8{ld16(X + (size_t)ch[k] * c + 8 * j)}.to(f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] += f[e];
         }
-        Y[i] = __float2bfloat16(acc * 0.125f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] *= 0.125f;
+        st16(Y + (size_t)pc * c + 8 * j, Bf8::from(acc).u);
     }
 }
 
-__global__ void avgpool_bwd(const bf16 *dY, Vol vi, int c, bf16 *dX)  // vi: input (fine) volume
+// gradient of the pooling: each fine position gets its parent's gradient / 8
+__global__ void avgpool_bwd(const bf16 *dY, Vol vi, int c, bf16 *dX)
 {
-    const long long n = vi.pos() * c, s = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += s) {
-        const int ch = (int)(i % c);
-        long long p = i / c;
-        const int x = (int)(p % vi.w); p /= vi.w;
-        const int y = (int)(p % vi.h); p /= vi.h;
-        const int z = (int)(p % vi.d);
-        const int b = (int)(p / vi.d);
-        const long long q = (((long long)b * (vi.d / 2) + z / 2) * (vi.h / 2) + y / 2) * (vi.w / 2) + x / 2;
-        dX[i] = __float2bfloat16(__bfloat162float(dY[q * c + ch]) * 0.125f);
+    const int c8 = c / 8, n = vi.n * vi.d * vi.h * vi.w * c8;
+    GRID_LOOP(i, n) {
+        const int p = i / c8, j = i - p * c8;
+        float f[8];
+        Bf8{ld16(dY + (size_t)parent_of(p, vi) * c + 8 * j)}.to(f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] *= 0.125f;
+        st16(dX + (size_t)p * c + 8 * j, Bf8::from(f).u);
     }
 }
 
-// nearest x2 upsampling of X (coarse, cx channels) into channels [0, cx) of a cdst-channel
-// fine volume, and the skip S (cs channels) into channels [cx, cx + cs)
+// nearest x2 upsampling of X (coarse, cx channels) into channels [0, cx) of the fine
+// volume vf, and the skip S (cs channels) into channels [cx, cx + cs)
 __global__ void upcat_fwd(const bf16 *X, int cx, const bf16 *S, int cs, Vol vf, bf16 *Y)
 {
-    const int c = cx + cs;
-    const long long n = vf.pos() * c, st = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
-        const int ch = (int)(i % c);
-        const long long p = i / c;
-        if (ch >= cx) {
-            Y[i] = S[p * cs + (ch - cx)];
-        } else {
-            long long q = p;
-            const int x = (int)(q % vf.w); q /= vf.w;
-            const int y = (int)(q % vf.h); q /= vf.h;
-            const int z = (int)(q % vf.d);
-            const int b = (int)(q / vf.d);
-            const long long pc = (((long long)b * (vf.d / 2) + z / 2) * (vf.h / 2) + y / 2) * (vf.w / 2) + x / 2;
-            Y[i] = X[pc * cx + ch];
-        }
+    const int c8 = (cx + cs) / 8, x8 = cx / 8, n = vf.n * vf.d * vf.h * vf.w * c8;
+    GRID_LOOP(i, n) {
+        const int p = i / c8, j = i - p * c8;
+        const uint4 v = j < x8 ? ld16(X + (size_t)parent_of(p, vf) * cx + 8 * j)
+                               : ld16(S + (size_t)p * cs + 8 * (j - x8));
+        st16(Y + (size_t)p * (cx + cs) + 8 * j, v);
     }
 }
 
-// gradient of upcat: the coarse part sums its 8 children; the skip part is copied
+// gradient of upcat, coarse part: each coarse position sums its 8 children
 __global__ void upcat_bwd_coarse(const bf16 *dY, int cx, int cs, Vol vc, bf16 *dX)
 {
-    const int c = cx + cs;
-    const long long n = vc.pos() * cx, st = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
-        const int ch = (int)(i % cx);
-        long long p = i / cx;
-        const int x = (int)(p % vc.w); p /= vc.w;
-        const int y = (int)(p % vc.h); p /= vc.h;
-        const int z = (int)(p % vc.d);
-        const int b = (int)(p / vc.d);
-        const int W = 2 * vc.w, H = 2 * vc.h, D = 2 * vc.d;
-        float acc = 0.f;
+    const int c = cx + cs, x8 = cx / 8, n = vc.n * vc.d * vc.h * vc.w * x8;
+    const Vol vf{vc.n, 2 * vc.d, 2 * vc.h, 2 * vc.w};
+    GRID_LOOP(i, n) {
+        const int pc = i / x8, j = i - pc * x8;
+        int ch[8];
+        children_of(pc, vf, ch);
+        float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const long long q = (((long long)b * D + 2 * z + (k >> 2)) * H + 2 * y + ((k >> 1) & 1)) * W + 2 * x + (k & 1);
-            acc += __bfloat162float(dY[q * c + ch]);
+            float f[8];
+            Bf8{ld16(dY + (size_t)ch[k] * c + 8 * j)}.to(f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] += f[e];
         }
-        dX[i] = __float2bfloat16(acc);
+        st16(dX + (size_t)pc * cx + 8 * j, Bf8::from(acc).u);
     }
 }
 
-__global__ void upcat_bwd_skip_add(const bf16 *dY, int cx, int cs, long long npos, bf16 *dS)
+// gradient of upcat, skip part, added to dS
+__global__ void upcat_bwd_skip_add(const bf16 *dY, int cx, int cs, int npos, bf16 *dS)
 {
-    const int c = cx + cs;
-    const long long n = npos * cs, st = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
-        const long long p = i / cs;
-        const int ch = (int)(i % cs);
-        dS[i] = __float2bfloat16(__bfloat162float(dS[i]) + __bfloat162float(dY[p * c + cx + ch]));
+    const int c = cx + cs, s8 = cs / 8, n = npos * s8;
+    GRID_LOOP(i, n) {
+        const int p = i / s8, j = i - p * s8;
+        float a[8], b[8];
+        Bf8{ld16(dS + (size_t)p * cs + 8 * j)}.to(a);
+        Bf8{ld16(dY + (size_t)p * c + cx + 8 * j)}.to(b);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] += b[e];
+        st16(dS + (size_t)p * cs + 8 * j, Bf8::from(a).u);
     }
 }
 
 // head: out[p] = x[p] + hb + sum_c hw[c] Y[p][c]
-__global__ void head_fwd(const bf16 *Y, const float *x, const float *hw, const float *hb,
-                         long long npos, float *out)
+__global__ void head_fwd(const bf16 *Y, const float *x, const float *hw, const float *hb, int npos, float *out)
 {
-    const long long st = (long long)gridDim.x * blockDim.x;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npos; p += st) {
+    GRID_LOOP(p, npos) {
+        float y[16];
+        Bf8{ld16(Y + 16 * (size_t)p)}.to(y);
+        Bf8{ld16(Y + 16 * (size_t)p + 8)}.to(y + 8);
         float s = hb[0];
-        for (int c = 0; c < 16; ++c) s += hw[c] * __bfloat162float(Y[p * 16 + c]);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) s += hw[c] * y[c];
         out[p] = x[p] + s;
     }
 }
 
 // loss L = mean (out - target)^2, dout = 2 (out - target) / n; dY = dout hw; head grads
-__global__ void head_bwd(const bf16 *Y, const float *out, const float *target, const float *hw,
-                         long long npos, bf16 *dY, float *dhw, float *dhb, float *loss)
+__global__ void head_bwd(const bf16 *Y, const float *out, const float *target, const float *hw, int npos,
+                         bf16 *dY, float *dhw, float *dhb, float *loss)
 {
     float gw[16] = {0}, gb = 0.f, l = 0.f;
     const float inv_n = 1.f / (float)npos;
-    const long long st = (long long)gridDim.x * blockDim.x;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npos; p += st) {
+    GRID_LOOP(p, npos) {
         const float e = out[p] - target[p];
         l += e * e * inv_n;
         const float d = 2.f * e * inv_n;
         gb += d;
+        float y[16], g[16];
+        Bf8{ld16(Y + 16 * (size_t)p)}.to(y);
+        Bf8{ld16(Y + 16 * (size_t)p + 8)}.to(y + 8);
+#pragma unroll
         for (int c = 0; c < 16; ++c) {
-            gw[c] += d * __bfloat162float(Y[p * 16 + c]);
-            dY[p * 16 + c] = __float2bfloat16(d * hw[c]);
+            gw[c] += d * y[c];
+            g[c] = d * hw[c];
         }
+        st16(dY + 16 * (size_t)p, Bf8::from(g).u);
+        st16(dY + 16 * (size_t)p + 8, Bf8::from(g + 8).u);
     }
     for (int o = 16; o > 0; o >>= 1) {
         l += __shfl_down_sync(0xffffffffu, l, o);
         gb += __shfl_down_sync(0xffffffffu, gb, o);
+#pragma unroll
         for (int c = 0; c < 16; ++c) gw[c] += __shfl_down_sync(0xffffffffu, gw[c], o);
     }
     if ((threadIdx.x & 31) == 0) {
@@ -585,30 +758,77 @@ unsigned grid1(long long n)
     return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32));
 }
 
-template <int COUT>
-cudaError_t launch_tc_t(const bf16 *X, int cin, const bf16 *W, const float *bias, Vol v, int relu,
-                        bf16 *Y, unsigned *err, cudaStream_t st)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
-    const int smem = tc_smem_bytes(cin, COUT);
-    cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_tc_t(const bf16 *X, const bf16 *W, const float *bias, Vol v, int relu, bf16 *Y,
+                        unsigned *err, cudaStream_t st)
+{
+    constexpr int cin = CIN;
+    if (v.w + 2 > 256 || tc_lines(v.w) > 256) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    // activations [n][d][h][w][cin] as a 5-D tensor, innermost first
+    CUtensorMap mx, mw;
+    const cuuint64_t xdim[5] = {(cuuint64_t)cin, (cuuint64_t)v.w, (cuuint64_t)v.h, (cuuint64_t)v.d, (cuuint64_t)v.n};
+    const cuuint64_t xstr[4] = {(cuuint64_t)cin * 2, (cuuint64_t)v.w * cin * 2, (cuuint64_t)v.h * v.w * cin * 2,
+                                (cuuint64_t)v.d * v.h * v.w * cin * 2};
+    const cuuint32_t xbox[5] = {8, (cuuint32_t)(v.w + 2), (cuuint32_t)tc_lines(v.w), 1, 1};
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(X), xdim, xstr, xbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    // weights [27 * cout][cin]
+    const cuuint64_t wdim[2] = {(cuuint64_t)cin, (cuuint64_t)27 * COUT};
+    const cuuint64_t wstr[1] = {(cuuint64_t)cin * 2};
+    const cuuint32_t wbox[2] = {8, (cuuint32_t)COUT};
+    if (enc(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(W), wdim, wstr, wbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const int ns = tc_stages(cin, COUT, v.w);
+    if (ns < 2) return cudaErrorInvalidValue;                   // the volume is too wide
+    const int smem = tc_smem_bytes(cin, COUT, v.w, ns);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = (unsigned)((v.pos() + kTcRows - 1) / kTcRows);
-    conv3d_fwd_tc<COUT><<<blocks, 128, smem, st>>>(X, cin, W, bias, v, relu, Y, err);
+    // resident CTAs per SM: shared memory (1 KiB per CTA reserved by the system), tensor
+    // memory (512 columns, two accumulators per CTA), threads
+    int dev = 0, sms = 0, smem_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    constexpr int ncol = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
+    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / (2 * ncol), 2048 / kTcThreads}));
+    const long long tiles = (long long)v.n * v.d * ((v.h * (v.w + 2) + kTcRows - 1) / kTcRows);
+    if (tiles * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per_sm));
+    conv3d_fwd_tc<CIN, COUT><<<blocks, kTcThreads, smem, st>>>(mx, mw, bias, v, relu, Y, err, ns);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_tc(const bf16 *X, int cin, const bf16 *W, const float *bias, Vol v, int cout,
                           int relu, bf16 *Y, unsigned *err, cudaStream_t st)
 {
-    if (cin % 16 || cin < 16 || cin > 96) return cudaErrorInvalidValue;
-    switch (cout) {
-    case 16: return launch_tc_t<16>(X, cin, W, bias, v, relu, Y, err, st);
-    case 32: return launch_tc_t<32>(X, cin, W, bias, v, relu, Y, err, st);
-    case 48: return launch_tc_t<48>(X, cin, W, bias, v, relu, Y, err, st);
-    case 64: return launch_tc_t<64>(X, cin, W, bias, v, relu, Y, err, st);
-    case 96: return launch_tc_t<96>(X, cin, W, bias, v, relu, Y, err, st);
-    default: return cudaErrorInvalidValue;
-    }
+    // the (cin, cout) pairs of the network's convolutions and of their input gradients
+#define MCX_TC(ci, co) \
+    if (cin == ci && cout == co) return launch_tc_t<ci, co>(X, W, bias, v, relu, Y, err, st);
+    MCX_TC(16, 16) MCX_TC(16, 32) MCX_TC(16, 48) MCX_TC(32, 16) MCX_TC(32, 32) MCX_TC(32, 64)
+    MCX_TC(32, 96) MCX_TC(48, 16) MCX_TC(64, 32) MCX_TC(64, 64) MCX_TC(96, 32)
+#undef MCX_TC
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bwd_w(const bf16 *X, int cin, const bf16 *dY, int cout, Vol v, float *dW,
@@ -715,27 +935,27 @@ static mcx_status forward(mcx_denoiser *d, const float *x, int n, float *out, cu
 {
     const Vol v0 = level_vol(d, 0, n), v1 = level_vol(d, 1, n), v2 = level_vol(d, 2, n);
     const float *P = d->params.as<float>();
-    pad_input<<<grid1(v0.pos() * 16), 256, 0, st>>>(x, v0.pos(), d->x16.as<bf16>());
+    pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, (int)v0.pos(), d->x16.as<bf16>());
     auto conv = [&](int l, const bf16 *in, Vol v) {
         return launch_fwd_tc(in, kLayers[l].cin, d->wf[l].as<bf16>(), P + d->b_off[l], v,
                              kLayers[l].cout, 1, d->a[l].as<bf16>(), d->status.as<unsigned>(), st);
     };
     DNC(d, conv(0, d->x16.as<bf16>(), v0), "conv e1a");
     DNC(d, conv(1, d->a[0].as<bf16>(), v0), "conv e1b");
-    avgpool_fwd<<<grid1(v1.pos() * 16), 256, 0, st>>>(d->a[1].as<bf16>(), v1, 16, d->p1.as<bf16>());
+    avgpool_fwd<<<grid1(v1.pos() * 2), 256, 0, st>>>(d->a[1].as<bf16>(), v1, 16, d->p1.as<bf16>());
     DNC(d, conv(2, d->p1.as<bf16>(), v1), "conv e2a");
     DNC(d, conv(3, d->a[2].as<bf16>(), v1), "conv e2b");
-    avgpool_fwd<<<grid1(v2.pos() * 32), 256, 0, st>>>(d->a[3].as<bf16>(), v2, 32, d->p2.as<bf16>());
+    avgpool_fwd<<<grid1(v2.pos() * 4), 256, 0, st>>>(d->a[3].as<bf16>(), v2, 32, d->p2.as<bf16>());
     DNC(d, conv(4, d->p2.as<bf16>(), v2), "conv ba");
     DNC(d, conv(5, d->a[4].as<bf16>(), v2), "conv bb");
-    upcat_fwd<<<grid1(v1.pos() * 96), 256, 0, st>>>(d->a[5].as<bf16>(), 64, d->a[3].as<bf16>(), 32, v1, d->u2.as<bf16>());
+    upcat_fwd<<<grid1(v1.pos() * 12), 256, 0, st>>>(d->a[5].as<bf16>(), 64, d->a[3].as<bf16>(), 32, v1, d->u2.as<bf16>());
     DNC(d, conv(6, d->u2.as<bf16>(), v1), "conv d2a");
     DNC(d, conv(7, d->a[6].as<bf16>(), v1), "conv d2b");
-    upcat_fwd<<<grid1(v0.pos() * 48), 256, 0, st>>>(d->a[7].as<bf16>(), 32, d->a[1].as<bf16>(), 16, v0, d->u1.as<bf16>());
+    upcat_fwd<<<grid1(v0.pos() * 6), 256, 0, st>>>(d->a[7].as<bf16>(), 32, d->a[1].as<bf16>(), 16, v0, d->u1.as<bf16>());
     DNC(d, conv(8, d->u1.as<bf16>(), v0), "conv d1a");
     DNC(d, conv(9, d->a[8].as<bf16>(), v0), "conv d1b");
     head_fwd<<<grid1(v0.pos()), 256, 0, st>>>(d->a[9].as<bf16>(), x, P + d->hw_off, P + d->hb_off,
-                                             v0.pos(), out);
+                                             (int)v0.pos(), out);
     DNC(d, cudaGetLastError(), "forward");
     return MCX_OK;
 }
@@ -747,8 +967,8 @@ static mcx_status conv_bwd(mcx_denoiser *d, int l, const bf16 *in, Vol v, bf16 *
     const LayerSpec &L = kLayers[l];
     float *G = d->grads.as<float>();
     bf16 *dA = d->ga[l].as<bf16>();
-    relu_mask<<<grid1(v.pos() * L.cout), 256, 0, st>>>(dA, d->a[l].as<bf16>(), v.pos() * L.cout);
-    bias_grad<<<dim3(64, L.cout), 256, 0, st>>>(dA, v.pos(), L.cout, G + d->b_off[l]);
+    relu_mask<<<grid1(v.pos() * L.cout / 8), 256, 0, st>>>(dA, d->a[l].as<bf16>(), (int)(v.pos() * L.cout / 8));
+    bias_grad<<<dim3(64, L.cout), 256, 0, st>>>(dA, (int)v.pos(), L.cout, G + d->b_off[l]);
     DNC(d, launch_bwd_w(in, L.cin, dA, L.cout, v, G + d->w_off[l], st), "weight gradient");
     if (dIn)
         DNC(d, launch_fwd_tc(dA, L.cout, d->wb[l].as<bf16>(), nullptr, v, L.cin, 0, dIn, d->status.as<unsigned>(), st),
@@ -764,25 +984,25 @@ static mcx_status backward(mcx_denoiser *d, const float *x, const float *target,
     DNC(d, cudaMemsetAsync(d->grads.p, 0, d->nparam * sizeof(float), st), "clearing gradients");
     DNC(d, cudaMemsetAsync(d->loss.p, 0, sizeof(float), st), "clearing the loss");
     head_bwd<<<grid1(v0.pos()), 256, 0, st>>>(d->a[9].as<bf16>(), d->out.as<float>(), target,
-                                             P + d->hw_off, v0.pos(), d->ga[9].as<bf16>(),
+                                             P + d->hw_off, (int)v0.pos(), d->ga[9].as<bf16>(),
                                              G + d->hw_off, G + d->hb_off, d->loss.as<float>());
     mcx_status s;
     if ((s = conv_bwd(d, 9, d->a[8].as<bf16>(), v0, d->ga[8].as<bf16>(), st)) != MCX_OK) return s;
     if ((s = conv_bwd(d, 8, d->u1.as<bf16>(), v0, d->gu1.as<bf16>(), st)) != MCX_OK) return s;
     // upcat 1: coarse part -> d2b output gradient, skip part -> e1b output gradient (later)
-    upcat_bwd_coarse<<<grid1(v1.pos() * 32), 256, 0, st>>>(d->gu1.as<bf16>(), 32, 16, v1, d->ga[7].as<bf16>());
+    upcat_bwd_coarse<<<grid1(v1.pos() * 4), 256, 0, st>>>(d->gu1.as<bf16>(), 32, 16, v1, d->ga[7].as<bf16>());
     if ((s = conv_bwd(d, 7, d->a[6].as<bf16>(), v1, d->ga[6].as<bf16>(), st)) != MCX_OK) return s;
     if ((s = conv_bwd(d, 6, d->u2.as<bf16>(), v1, d->gu2.as<bf16>(), st)) != MCX_OK) return s;
-    upcat_bwd_coarse<<<grid1(v2.pos() * 64), 256, 0, st>>>(d->gu2.as<bf16>(), 64, 32, v2, d->ga[5].as<bf16>());
+    upcat_bwd_coarse<<<grid1(v2.pos() * 8), 256, 0, st>>>(d->gu2.as<bf16>(), 64, 32, v2, d->ga[5].as<bf16>());
     if ((s = conv_bwd(d, 5, d->a[4].as<bf16>(), v2, d->ga[4].as<bf16>(), st)) != MCX_OK) return s;
     if ((s = conv_bwd(d, 4, d->p2.as<bf16>(), v2, d->gp2.as<bf16>(), st)) != MCX_OK) return s;
     // e2b output gradient = pool backward + the skip part of upcat 2
-    avgpool_bwd<<<grid1(v1.pos() * 32), 256, 0, st>>>(d->gp2.as<bf16>(), v1, 32, d->ga[3].as<bf16>());
-    upcat_bwd_skip_add<<<grid1(v1.pos() * 32), 256, 0, st>>>(d->gu2.as<bf16>(), 64, 32, v1.pos(), d->ga[3].as<bf16>());
+    avgpool_bwd<<<grid1(v1.pos() * 4), 256, 0, st>>>(d->gp2.as<bf16>(), v1, 32, d->ga[3].as<bf16>());
+    upcat_bwd_skip_add<<<grid1(v1.pos() * 4), 256, 0, st>>>(d->gu2.as<bf16>(), 64, 32, (int)v1.pos(), d->ga[3].as<bf16>());
     if ((s = conv_bwd(d, 3, d->a[2].as<bf16>(), v1, d->ga[2].as<bf16>(), st)) != MCX_OK) return s;
     if ((s = conv_bwd(d, 2, d->p1.as<bf16>(), v1, d->gp1.as<bf16>(), st)) != MCX_OK) return s;
-    avgpool_bwd<<<grid1(v0.pos() * 16), 256, 0, st>>>(d->gp1.as<bf16>(), v0, 16, d->ga[1].as<bf16>());
-    upcat_bwd_skip_add<<<grid1(v0.pos() * 16), 256, 0, st>>>(d->gu1.as<bf16>(), 32, 16, v0.pos(), d->ga[1].as<bf16>());
+    avgpool_bwd<<<grid1(v0.pos() * 2), 256, 0, st>>>(d->gp1.as<bf16>(), v0, 16, d->ga[1].as<bf16>());
+    upcat_bwd_skip_add<<<grid1(v0.pos() * 2), 256, 0, st>>>(d->gu1.as<bf16>(), 32, 16, (int)v0.pos(), d->ga[1].as<bf16>());
     if ((s = conv_bwd(d, 1, d->a[0].as<bf16>(), v0, d->ga[0].as<bf16>(), st)) != MCX_OK) return s;
     if ((s = conv_bwd(d, 0, d->x16.as<bf16>(), v0, nullptr, st)) != MCX_OK) return s;
     DNC(d, cudaGetLastError(), "backward");
@@ -796,8 +1016,11 @@ mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uin
 {
     if (!out) return dn_fail(nullptr, MCX_E_ARG, "out is NULL");
     *out = nullptr;
-    if (nx % 64 || nx < 64 || ny % 4 || nz % 4 || ny < 4 || nz < 4 || max_batch < 1)
-        return dn_fail(nullptr, MCX_E_ARG, "need nx a multiple of 64, ny and nz multiples of 4, max_batch >= 1");
+    if (nx % 64 || nx < 64 || nx > 252 || ny % 4 || nz % 4 || ny < 4 || nz < 4 || max_batch < 1)
+        return dn_fail(nullptr, MCX_E_ARG,
+                       "need nx a multiple of 64 up to 252, ny and nz multiples of 4, max_batch >= 1");
+    if ((unsigned long long)max_batch * nx * ny * nz * 96ull >= (1ull << 31))
+        return dn_fail(nullptr, MCX_E_ARG, "max_batch * nx * ny * nz * 96 must stay below 2^31");
     mcx_denoiser *d = new (std::nothrow) mcx_denoiser();
     if (!d) return dn_fail(nullptr, MCX_E_OOM, "host allocation failed");
     d->D = (int)nz; d->H = (int)ny; d->W = (int)nx; d->maxb = (int)max_batch;
