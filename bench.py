@@ -297,18 +297,24 @@ def study_denoise(args):
     ms_tg = dn.simulate(train_v, args.dn_target, phi_tg, seed_offset=1_000_003)
     gen_s = time.time() - t0
     maxb = max(args.dn_batch, 16)
-    d = mcx.Denoiser(shape, max_batch=maxb, seed=args.dn_seed)
+    n_aux = args.dn_aux
+    d = mcx.Denoiser(shape, max_batch=maxb, seed=args.dn_seed, n_aux=n_aux)
     x_set, t_set = torch.empty_like(phi_in), torch.empty_like(phi_tg)
     dn.encode_set(d, phi_in, x_set)
     dn.encode_set(d, phi_tg, t_set)
     del phi_in, phi_tg
+    aux_set = None
+    if n_aux:
+        aux_set = torch.empty((len(train_v), 2) + shape, device=dev)
+        dn.features(train_v, aux_set)
     torch.cuda.synchronize()
     t1 = time.time()
     losses = dn.train(d, x_set, t_set, args.dn_steps, args.dn_batch, lr=args.dn_lr,
-                      lr_final=args.dn_lr / 10, seed=args.dn_seed, log_every=max(args.dn_steps // 10, 1))
+                      lr_final=args.dn_lr / 10, seed=args.dn_seed, log_every=max(args.dn_steps // 10, 1),
+                      aux_set=aux_set)
     torch.cuda.synchronize()
     train_s = time.time() - t1
-    del x_set, t_set
+    del x_set, t_set, aux_set
 
     # held-out evaluation
     n_t = len(test_v)
@@ -328,12 +334,16 @@ def study_denoise(args):
             low_in = low.clone()
             walk_in_ms = ms
     out = torch.empty_like(ref)
-    dn.denoise(d, low_in, out)                     # warm-up
+    aux_t = None
+    if n_aux:
+        aux_t = torch.empty((n_t, 2) + shape, device=dev)
+        dn.features(test_v, aux_t)
+    dn.denoise(d, low_in, out, aux=aux_t)          # warm-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
     e0.record()
     for _ in range(reps):
-        dn.denoise(d, low_in, out)
+        dn.denoise(d, low_in, out, aux=aux_t)
     e1.record()
     e1.synchronize()
     d.sync()
@@ -363,6 +373,7 @@ def study_denoise(args):
     tflops = fwd_flop * n_t / (apply_ms * 1e-3) / 1e12
     print(json.dumps({
         "study": "denoise", "volumes": "64x64x64 mm, 1-3 ellipsoids, random optics (c5)",
+        "feature_channels": n_aux,
         "train_volumes": len(train_v), "test_volumes": n_t, "photons_input": args.dn_in,
         "photons_target": args.dn_target, "photons_reference": args.dn_ref,
         "data_walk_ms": ms_in + ms_tg, "data_wall_s": gen_s,
@@ -456,6 +467,8 @@ def main():
     ap.add_argument("--dn-batch", type=int, default=4)
     ap.add_argument("--dn-lr", type=float, default=1e-3)
     ap.add_argument("--dn-seed", type=int, default=7)
+    ap.add_argument("--dn-aux", type=int, default=0, choices=[0, 2],
+                    help="medium-feature input channels (log mua, log reduced mus)")
     args = ap.parse_args()
 
     world, rank, local = dist_env()

@@ -320,7 +320,8 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
    stays the fallback: the denoiser never replaces the walk, it post-processes its map.
 
    Network (a U-Net; all 3x3x3 convolutions have a bias and ReLU, "same" zero padding):
-     level 0 (nz,ny,nx):   e1a 1->16 (the input channel zero-padded to 16), e1b 16->16
+     level 0 (nz,ny,nx):   e1a 16->16 (input channel 0: the encoded fluence; channels
+                           1..n_aux: medium features; the rest zero), e1b 16->16
      2x2x2 average pool;   level 1: e2a 16->32, e2b 32->32
      2x2x2 average pool;   level 2: ba 32->64, bb 64->64
      nearest x2 upsample, concatenated with e2b's output (upsampled channels first):
@@ -336,7 +337,9 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
    The network domain: x = (log10(max(phi, 0) + floor) - mu) / sigma, with the inverse
    phi = max(10^(x sigma + mu) - floor, 0); defaults floor 1e-8, mu -4, sigma 2.
 
-   Volumes are FP32 [n][nz][ny][nx] device arrays on the denoiser's device, n <= max_batch.
+   Volumes are FP32 [n][nz][ny][nx] device arrays on the denoiser's device, n <= max_batch;
+   medium features (when n_aux > 0) are FP32 [n][n_aux][nz][ny][nx] (mcx_denoiser_features
+   computes the two this library defines from a label volume).
    Sizes: nx a multiple of 64 up to 252 (so nx = 64 or 128), ny and nz multiples of 4,
    max_batch * nx * ny * nz * 96 < 2^31.  The object owns every buffer it
    needs (activations for max_batch volumes); calls on one object must not overlap.
@@ -344,10 +347,10 @@ mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, 
    mcx_denoiser_sync), described by mcx_last_error(NULL). */
 typedef struct mcx_denoiser mcx_denoiser;
 
-/* He-normal weights drawn from `seed`, zero biases and a zero head (the untrained network
-   returns its input). */
+/* n_aux = 0..7 medium-feature input channels.  He-normal weights drawn from `seed`, zero
+   biases and a zero head (the untrained network returns its input). */
 mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uint32_t nz,
-                               uint32_t max_batch, uint64_t seed);
+                               uint32_t max_batch, uint32_t n_aux, uint64_t seed);
 mcx_status mcx_denoiser_param_count(const mcx_denoiser *d, uint64_t *n);
 /* which = 0: the FP32 master weights; which = 1: the gradients of the last train step.
    Waits for the device. */
@@ -355,23 +358,31 @@ mcx_status mcx_denoiser_get_params(mcx_denoiser *d, float *host, uint64_t n, int
 /* Replaces the weights (and resets the optimizer state). Waits for the device. */
 mcx_status mcx_denoiser_set_params(mcx_denoiser *d, const float *host, uint64_t n);
 mcx_status mcx_denoiser_set_encoding(mcx_denoiser *d, float floor_, float mu, float sigma);
-/* Network domain in and out: y_dev = net(x_dev) for n volumes, enqueued on `stream`. */
-mcx_status mcx_denoiser_forward(mcx_denoiser *d, const float *x_dev, float *y_dev, uint32_t n,
-                                void *stream);
+/* Network domain in and out: y_dev = net(x_dev, aux_dev) for n volumes, enqueued on
+   `stream`; aux_dev may be NULL when n_aux = 0. */
+mcx_status mcx_denoiser_forward(mcx_denoiser *d, const float *x_dev, const float *aux_dev,
+                                float *y_dev, uint32_t n, void *stream);
 /* One training step on n (input, target) pairs in the network domain: loss = mean over all
    voxels of (net(x) - t)^2, gradients of every parameter, then (if lr > 0) one Adam step
    (beta 0.9 / 0.999, eps 1e-8).  With loss_host non-NULL the call waits and returns the
    loss there. */
-mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const float *t_dev,
-                                   uint32_t n, float lr, float *loss_host, void *stream);
+mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const float *aux_dev,
+                                   const float *t_dev, uint32_t n, float lr, float *loss_host,
+                                   void *stream);
 /* Elementwise maps between fluence and the network domain (count values). */
 mcx_status mcx_denoiser_encode(mcx_denoiser *d, const float *phi_dev, float *x_dev,
                                uint64_t count, void *stream);
 mcx_status mcx_denoiser_decode(mcx_denoiser *d, const float *x_dev, float *phi_dev,
                                uint64_t count, void *stream);
 /* Denoises n fluence maps: encode, forward, decode, enqueued on `stream`. */
-mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, float *phi_out_dev,
-                              uint32_t n, void *stream);
+mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, const float *aux_dev,
+                              float *phi_out_dev, uint32_t n, void *stream);
+/* The two medium features of a label volume (uint8 [nvox] on the device; props as in
+   mcx_set_media, label l -> row l, labels >= n_media count as exterior):
+   out_dev[0][v] = log10(max(mua, 1e-4)) + 2, out_dev[1][v] = log10(max(mus (1 - g), 1e-3))
+   (FP32 [2][nvox]).  Waits for `stream`. */
+mcx_status mcx_denoiser_features(const uint8_t *labels_dev, uint64_t nvox, uint32_t n_media,
+                                 const float *props, float *out_dev, void *stream);
 /* Builds a training batch: volume s of dst_dev (n volumes) is volume idx[s] of set_dev
    (set_count volumes of the denoiser's shape), mirrored in x (flags[s] bit 0) and in y
    (bit 1), then transposed in x/y (bit 2; needs ny == nx).  idx and flags are host arrays

@@ -20,8 +20,10 @@ Parity status (what pins each function, tests/test_denoiser_oracle.py):
   * bf16_round: hand-checked values (ties to even, carries, signs).
   * conv3d: brute-force nested loops on tiny inputs; torch.nn.functional.conv3d.
   * avg_pool2 / upsample2: adjointness (<pool x, y> = <x, up y> / 8), constants.
-  * forward: zero head returns the input; the one-layer case against brute force;
-    equivariance under shifts by 4 voxels away from the boundary.
+  * forward: zero head returns the input; the one-layer case against brute force (with
+    and without feature channels); equivariance under shifts by 4 voxels away from the
+    boundary.
+  * features: hand-computed values for a two-label table and the exterior.
   * loss_and_grads: central finite differences of the exact FP64 loss.
   * adam: the closed form of the first step (|update| = lr for non-zero gradients).
 """
@@ -110,8 +112,10 @@ def upsample2(x: torch.Tensor) -> torch.Tensor:
     return x.repeat_interleave(2, 1).repeat_interleave(2, 2).repeat_interleave(2, 3)
 
 
-def forward(params, x, bf16: bool = True) -> torch.Tensor:
-    """x [n, nz, ny, nx] (network domain) -> y [n, nz, ny, nx]; y = x + head(U-Net(x))."""
+def forward(params, x, bf16: bool = True, aux=None) -> torch.Tensor:
+    """x [n, nz, ny, nx] (network domain), optional medium features aux [n, k, nz, ny, nx]
+    -> y [n, nz, ny, nx]; y = x + head(U-Net(x, aux)).  The input layer sees x as channel
+    0 and the k features as channels 1..k of 16 (the rest zero)."""
     P = unpack(params) if not isinstance(params, dict) else params
     x = torch.as_tensor(np.asarray(x) if not torch.is_tensor(x) else x, dtype=torch.float64)
     q = lambda t: _ste(t, bf16)
@@ -119,7 +123,13 @@ def forward(params, x, bf16: bool = True) -> torch.Tensor:
     def conv(name, a):
         return q(torch.relu(conv3d(a, q(P[name + ".w"]), P[name + ".b"])))
 
-    x16 = torch.cat([q(x)[..., None], torch.zeros(x.shape + (15,), dtype=torch.float64)], dim=-1)
+    k = 0 if aux is None else aux.shape[1]
+    feats = [q(x)[..., None]]
+    if k:
+        a = torch.as_tensor(np.asarray(aux), dtype=torch.float64)
+        feats.append(q(a.permute(0, 2, 3, 4, 1)))
+    feats.append(torch.zeros(x.shape + (15 - k,), dtype=torch.float64))
+    x16 = torch.cat(feats, dim=-1)
     a0 = conv("e1a", x16)
     a1 = conv("e1b", a0)
     p1 = q(avg_pool2(a1))
@@ -137,11 +147,11 @@ def forward(params, x, bf16: bool = True) -> torch.Tensor:
     return x + P["hb"][0] + torch.einsum("nzyxc,c->nzyx", a9, P["hw"])
 
 
-def loss_and_grads(params, x, t, bf16: bool = True):
+def loss_and_grads(params, x, t, bf16: bool = True, aux=None):
     """loss = mean (forward(x) - t)^2 over every voxel of the batch, and d loss / d params
     as a flat float64 vector in the parameter layout."""
     p = torch.tensor(np.asarray(params, dtype=np.float64), requires_grad=True)
-    y = forward(unpack(p), x, bf16=bf16)
+    y = forward(unpack(p), x, bf16=bf16, aux=aux)
     tt = torch.as_tensor(np.asarray(t), dtype=torch.float64)
     loss = ((y - tt) ** 2).mean()
     loss.backward()
@@ -166,6 +176,18 @@ def encode(phi, floor=1e-8, mu=-4.0, sigma=2.0):
 def decode(x, floor=1e-8, mu=-4.0, sigma=2.0):
     """network domain -> fluence"""
     return np.maximum(10.0 ** (np.asarray(x, dtype=np.float64) * sigma + mu) - floor, 0)
+
+
+def features(labels, media):
+    """the two medium features per voxel: log10(max(mua, 1e-4)) + 2 and
+    log10(max(mus (1 - g), 1e-3)); labels beyond the table count as exterior"""
+    m = np.asarray(media, dtype=np.float64).reshape(-1, 4)
+    f0 = np.log10(np.maximum(m[:, 0], 1e-4)) + 2.0
+    f1 = np.log10(np.maximum(m[:, 1] * (1.0 - m[:, 2]), 1e-3))
+    lab = np.asarray(labels).astype(np.int64)
+    ok = lab < len(m)
+    l = np.where(ok, lab, 0)
+    return np.stack([np.where(ok, f0[l], -2.0), np.where(ok, f1[l], -3.0)])
 
 
 def log_rms(phi, phi_ref, floor=1e-8, rel_mask=1e-6) -> float:

@@ -136,16 +136,17 @@ SIGNATURES = {
     "mcx_batch_size": (_i32, [_P]),
     "mcx_batch_last_error": (ctypes.c_char_p, [_P]),
     "mcx_batch_destroy": (None, [_P]),
-    "mcx_denoiser_create": (_i32, [ctypes.POINTER(_P), _u32, _u32, _u32, _u32, _u64]),
+    "mcx_denoiser_create": (_i32, [ctypes.POINTER(_P), _u32, _u32, _u32, _u32, _u32, _u64]),
     "mcx_denoiser_param_count": (_i32, [_P, ctypes.POINTER(_u64)]),
     "mcx_denoiser_get_params": (_i32, [_P, _P, _u64, _i32]),
     "mcx_denoiser_set_params": (_i32, [_P, _P, _u64]),
     "mcx_denoiser_set_encoding": (_i32, [_P, _f32, _f32, _f32]),
-    "mcx_denoiser_forward": (_i32, [_P, _P, _P, _u32, _P]),
-    "mcx_denoiser_train_step": (_i32, [_P, _P, _P, _u32, _f32, ctypes.POINTER(_f32), _P]),
+    "mcx_denoiser_forward": (_i32, [_P, _P, _P, _P, _u32, _P]),
+    "mcx_denoiser_train_step": (_i32, [_P, _P, _P, _P, _u32, _f32, ctypes.POINTER(_f32), _P]),
     "mcx_denoiser_encode": (_i32, [_P, _P, _P, _u64, _P]),
     "mcx_denoiser_decode": (_i32, [_P, _P, _P, _u64, _P]),
-    "mcx_denoiser_apply": (_i32, [_P, _P, _P, _u32, _P]),
+    "mcx_denoiser_apply": (_i32, [_P, _P, _P, _P, _u32, _P]),
+    "mcx_denoiser_features": (_i32, [_P, _u64, _u32, _P, _P, _P]),
     "mcx_denoiser_gather": (_i32, [_P, _P, _u64, _P, _P, _u32, _P, _P]),
     "mcx_denoiser_sync": (_i32, [_P]),
     "mcx_denoiser_destroy": (None, [_P]),
@@ -608,16 +609,17 @@ class Simulation:
 
 class Denoiser:
     """The learned fluence denoiser (mcx_denoiser_* in include/mcx.h).  Volumes are torch
-    CUDA tensors of shape [n, nz, ny, nx] (float32, contiguous); the stream defaults to
-    torch's current stream."""
+    CUDA tensors of shape [n, nz, ny, nx] (float32, contiguous), medium features
+    [n, n_aux, nz, ny, nx]; the stream defaults to torch's current stream."""
 
-    def __init__(self, shape, max_batch: int = 1, seed: int = 0):
+    def __init__(self, shape, max_batch: int = 1, seed: int = 0, n_aux: int = 0):
         nz, ny, nx = shape
         h = ctypes.c_void_p()
-        _check(None, load().mcx_denoiser_create(ctypes.byref(h), nx, ny, nz, max_batch, seed))
+        _check(None, load().mcx_denoiser_create(ctypes.byref(h), nx, ny, nz, max_batch, n_aux, seed))
         self.handle = h
         self.shape = (nz, ny, nx)
         self.max_batch = max_batch
+        self.n_aux = n_aux
         n = ctypes.c_uint64()
         _check(None, load().mcx_denoiser_param_count(self.handle, ctypes.byref(n)))
         self.n_params = n.value
@@ -654,16 +656,24 @@ class Denoiser:
     def set_encoding(self, floor: float, mu: float, sigma: float):
         _check(None, load().mcx_denoiser_set_encoding(self.handle, floor, mu, sigma))
 
-    def forward(self, x, y, stream=None):
+    def _aux(self, aux, n):
+        if not self.n_aux:
+            return None
+        if aux is None or tuple(aux.shape) != (n, self.n_aux) + self.shape or not aux.is_contiguous():
+            raise ValueError(f"need medium features [n, {self.n_aux}, {self.shape}]")
+        return _ptr(aux)
+
+    def forward(self, x, y, aux=None, stream=None):
         n = self._vol(x)
         self._vol(y)
-        _check(None, load().mcx_denoiser_forward(self.handle, _ptr(x), _ptr(y), n, self._stream(stream)))
+        _check(None, load().mcx_denoiser_forward(self.handle, _ptr(x), self._aux(aux, n), _ptr(y), n,
+                                                 self._stream(stream)))
 
-    def train_step(self, x, t, lr: float, stream=None) -> float:
+    def train_step(self, x, t, lr: float, aux=None, stream=None) -> float:
         n = self._vol(x)
         self._vol(t)
         loss = ctypes.c_float()
-        _check(None, load().mcx_denoiser_train_step(self.handle, _ptr(x), _ptr(t), n, lr,
+        _check(None, load().mcx_denoiser_train_step(self.handle, _ptr(x), self._aux(aux, n), _ptr(t), n, lr,
                                                     ctypes.byref(loss), self._stream(stream)))
         return loss.value
 
@@ -675,11 +685,21 @@ class Denoiser:
         _check(None, load().mcx_denoiser_decode(self.handle, _ptr(x), _ptr(phi), x.numel(),
                                                 self._stream(stream)))
 
-    def apply(self, phi_in, phi_out, stream=None):
+    def apply(self, phi_in, phi_out, aux=None, stream=None):
         n = self._vol(phi_in)
         self._vol(phi_out)
-        _check(None, load().mcx_denoiser_apply(self.handle, _ptr(phi_in), _ptr(phi_out), n,
+        _check(None, load().mcx_denoiser_apply(self.handle, _ptr(phi_in), self._aux(aux, n), _ptr(phi_out), n,
                                                self._stream(stream)))
+
+    @staticmethod
+    def features(labels_dev, media, out, stream=None):
+        """the two medium features of a label volume (torch uint8 CUDA tensor) into out
+        (float32 CUDA tensor of 2 * labels.numel() values); see mcx_denoiser_features"""
+        a = np.ascontiguousarray(media, dtype=np.float32).reshape(-1, 4)
+        if out.numel() != 2 * labels_dev.numel():
+            raise ValueError("out must hold 2 values per voxel")
+        _check(None, load().mcx_denoiser_features(_ptr(labels_dev), labels_dev.numel(), a.shape[0], _ptr(a),
+                                                  _ptr(out), Denoiser._stream(stream)))
 
     def gather(self, volumes, idx, flags, out, stream=None):
         """out[s] = transformed volumes[idx[s]] (see mcx_denoiser_gather)"""

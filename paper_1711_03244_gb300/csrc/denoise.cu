@@ -209,18 +209,20 @@ __device__ __forceinline__ void tc_commit(uint32_t bar)
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kTcThreads)
 conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
-              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err, int ns)
+              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err, int ns,
+              int zc)
 {
     constexpr int cin = CIN;
     constexpr bool WALL = tc_wall(CIN, COUT);
     constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns per accumulator
+    constexpr int NSLOT = WALL ? 4 : 2;                                // accumulators per CTA
     constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
-    // header: full[ns] at 0, empty[ns] at 64, acc full[2] at 128, acc empty[2] at 144,
-    // weights barrier at 160, TMEM address at 192
-    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 144, wbar = base + 160;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 192 - smem_u32(smem_raw)));
+    // header: full[ns] at 0, empty[ns] at 64, acc full[4] at 128, acc empty[4] at 160,
+    // weights barrier at 192, TMEM address at 224
+    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 160, wbar = base + 192;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 224 - smem_u32(smem_raw)));
     const int wtap = COUT * cin * 2, lbo_b = COUT * 16;
     const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
     const int a_bytes = (cin / 8) * lbo_a;
@@ -228,14 +230,24 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     const uint32_t ring = wres + (WALL ? 27 * wtap : 0);
     const int stage_bytes = a_bytes + (WALL ? 0 : 9 * wtap);
     const int tid = threadIdx.x, warp = tid >> 5;
+    // work units: columns of up to zc tiles at the same q0 in consecutive planes
     const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
-    const int n_tiles = v.n * v.d * tiles_plane;
-    const int my_tiles = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int n_steps = my_tiles * 3;
+    const int cols_z = (v.d + zc - 1) / zc;
+    const int n_units = v.n * cols_z * tiles_plane;
+    const int my_units = n_units > (int)blockIdx.x ? (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    struct Unit { int b, z0, nz, q0; };
+    auto unit_of = [&](int j) {
+        const int u = (int)blockIdx.x + j * (int)gridDim.x;
+        const int k = u % tiles_plane, r = u / tiles_plane;
+        const int z0 = (r % cols_z) * zc;
+        return Unit{r / cols_z, z0, min(zc, v.d - z0), k * kTcRows};
+    };
+    // first window line: one above the line of q0 - 1
+    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     ::"r"(smem_u32(tslot)), "r"(2 * NCOL) : "memory");
+                     ::"r"(smem_u32(tslot)), "r"(NSLOT * NCOL) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
@@ -243,7 +255,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
             mbar_init(full0 + 8 * b, 1);
             mbar_init(empty0 + 8 * b, 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NSLOT; ++a) {
             mbar_init(accf0 + 8 * a, 1);
             mbar_init(acce0 + 8 * a, 4 * 32);
         }
@@ -256,21 +268,11 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     const uint32_t tmem = *tslot;
     bool ok = true;
 
-    auto tile_q0 = [&](int t, int &b, int &z) {              // local tile t -> (volume, plane, q0)
-        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
-        const int plane = tile / tiles_plane;
-        z = plane % v.d;
-        b = plane / v.d;
-        return (tile % tiles_plane) * kTcRows;
-    };
-    // first window line: one above the line of q0 - 1
-    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
-
     if (tid == 0) {
         // ------------------------------------------------------------ producer (TMA)
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
         asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
-        if (WALL && n_steps) {
+        if (WALL && my_units) {
             mbar_expect_tx(wbar, 27 * wtap);
             for (int tap = 0; tap < 27; ++tap)
                 for (int c = 0; c < cin / 8; ++c)
@@ -278,101 +280,114 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
         }
         const uint32_t tx = a_bytes / lbo_a * (L * PW * 16) + (WALL ? 0 : 9 * wtap);
         int b = 0, use = 0;
-        for (int s = 0; s < n_steps && ok; ++s) {
-            if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
-            if (!ok) break;
-            int vb, z;
-            const int q0 = tile_q0(s / 3, vb, z);
-            const int g = s % 3;                               // plane z + g - 1
-            const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
-            mbar_expect_tx(fb, tx);
-            for (int c = 0; c < cin / 8; ++c)
-                tma_load_5d(st + c * lbo_a, &tmx, 8 * c, -1, first_line(q0), z + g - 1, vb, fb);
-            if (!WALL)
-                for (int tt = 0; tt < 9; ++tt)
-                    for (int c = 0; c < cin / 8; ++c)
-                        tma_load_2d(st + a_bytes + tt * wtap + c * lbo_b, &tmw, 8 * c, (9 * g + tt) * COUT, fb);
-            if (++b == ns) { b = 0; ++use; }
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            const Unit U = unit_of(uj);
+            const int fl = first_line(U.q0);
+            for (int j = 0; j < U.nz + 2 && ok; ++j) {        // window of plane z0 - 1 + j
+                if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
+                if (!ok) break;
+                const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
+                mbar_expect_tx(fb, tx);
+                for (int c = 0; c < cin / 8; ++c)
+                    tma_load_5d(st + c * lbo_a, &tmx, 8 * c, -1, fl, U.z0 - 1 + j, U.b, fb);
+                if (!WALL)                                       // one tile per unit: dz = j - 1
+                    for (int tt = 0; tt < 9; ++tt)
+                        for (int c = 0; c < cin / 8; ++c)
+                            tma_load_2d(st + a_bytes + tt * wtap + c * lbo_b, &tmw, 8 * c, (9 * j + tt) * COUT, fb);
+                if (++b == ns) { b = 0; ++use; }
+            }
         }
         // every load issued has landed before the CTA may exit
         for (int bb = 0; bb < ns; ++bb) {
             const int issued = use + (bb < b ? 1 : 0);       // fills of buffer bb
             if (issued > 0) ok &= mbar_wait(full0 + 8 * bb, (uint32_t)((issued - 1) & 1));
         }
-        if (WALL && n_steps) ok &= mbar_wait(wbar, 0);
+        if (WALL && my_units) ok &= mbar_wait(wbar, 0);
     } else if (tid == 32) {
         // ------------------------------------------------------------ MMA issuer
-        if (WALL && n_steps) ok &= mbar_wait(wbar, 0);
+        if (WALL && my_units) ok &= mbar_wait(wbar, 0);
         const uint64_t adesc0 = umma_desc(ring, lbo_a, 128);
         const uint64_t bdesc0 = umma_desc(WALL ? wres : ring + a_bytes, lbo_b, 128);
         int toff[9];                                            // row offset of each (dy, dx) tap
 #pragma unroll
         for (int tt = 0; tt < 9; ++tt) toff[tt] = (tt / 3 - 1) * PW + (tt % 3 - 1);
-        int b = 0, use = 0;
-        for (int s = 0; s < n_steps && ok; ++s) {
-            const int t = s / 3, g = s % 3, acc = t & 1;
-            if (g == 0 && t >= 2) ok &= mbar_wait(acce0 + 8 * acc, (uint32_t)(((t >> 1) - 1) & 1));
-            ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
-            if (!ok) break;
-            tc_fence_after();
-            int vb, z;
-            const int q0 = tile_q0(t, vb, z);
-            const int off = q0 - first_line(q0) * PW;           // window row of q0
-            // descriptors differ only in the start-address field (address / 16, 14 bits;
-            // every address here is below 256 KiB), so each instruction's pair is the
-            // stage's base descriptor plus a constant offset
-            const uint64_t abase = adesc0 + (uint64_t)((b * stage_bytes + off * 16) >> 4);
-            const uint64_t bbase = bdesc0 + (uint64_t)((WALL ? 9 * g * wtap : b * stage_bytes) >> 4);
-            const uint32_t d = tmem + acc * NCOL;
+        int b = 0, use = 0, T0 = 0;                             // T0: tiles of earlier units
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            const Unit U = unit_of(uj);
+            const int off = U.q0 - first_line(U.q0) * PW;      // window row of q0
+            for (int j = 0; j < U.nz + 2 && ok; ++j) {
+                ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
+                if (!ok) break;
+                tc_fence_after();
+                // descriptors differ only in the start-address field (address / 16, 14 bits;
+                // every address here is below 256 KiB): base descriptor plus an offset
+                const uint64_t abase = adesc0 + (uint64_t)((b * stage_bytes + off * 16) >> 4);
+                // tiles i of the unit reading this plane, the finishing one first: dz = j - 1 - i
+                for (int i = j - 2; i <= j; ++i) {
+                    if (i < 0 || i >= U.nz) continue;
+                    const int dz = j - 1 - i, T = T0 + i, slot = T & (NSLOT - 1);
+                    if (dz == -1 && T >= NSLOT)                 // the slot's previous tile is read out
+                        ok &= mbar_wait(acce0 + 8 * slot, (uint32_t)((T / NSLOT - 1) & 1));
+                    if (!ok) break;
+                    const uint64_t bbase = WALL ? bdesc0 + (uint64_t)((9 * (dz + 1) * wtap) >> 4)
+                                                : bdesc0 + (uint64_t)((b * stage_bytes) >> 4);
+                    const uint32_t d = tmem + slot * NCOL;
 #pragma unroll
-            for (int tt = 0; tt < 9; ++tt)                      // tt = 3 (dy + 1) + (dx + 1)
+                    for (int tt = 0; tt < 9; ++tt)              // tt = 3 (dy + 1) + (dx + 1)
 #pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk) {
-                    const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
-                    const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
-                    const uint32_t accum = (g | tt | kk) ? 1u : 0u;
-                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                 ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                            const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
+                            const uint32_t accum = (dz == -1 && tt == 0 && kk == 0) ? 0u : 1u;
+                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                         ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
+                        }
+                    if (dz == 1) tc_commit(accf0 + 8 * slot);    // tile i is complete
                 }
-            tc_commit(empty0 + 8 * b);
-            if (g == 2) tc_commit(accf0 + 8 * acc);
-            if (++b == ns) { b = 0; ++use; }
+                tc_commit(empty0 + 8 * b);
+                if (++b == ns) { b = 0; ++use; }
+            }
+            T0 += U.nz;
         }
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
-        for (int t = 0; t < my_tiles && ok; ++t) {
-            const int acc = t & 1;
-            ok &= mbar_wait(accf0 + 8 * acc, (uint32_t)((t >> 1) & 1));
-            ok = __all_sync(0xffffffffu, ok);                   // the collective reads below
-            if (!ok) break;
-            tc_fence_after();
-            float a[COUT];
-            const uint32_t taddr = tmem + acc * NCOL + ((uint32_t)(quarter * 32) << 16);
+        int T = 0;
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            const Unit U = unit_of(uj);
+            const int q = U.q0 + r, y = q / PW, x = q - y * PW - 1;
+            const bool valid = y < v.h && x >= 0 && x < v.w;
+            for (int i = 0; i < U.nz && ok; ++i, ++T) {
+                const int slot = T & (NSLOT - 1);
+                ok &= mbar_wait(accf0 + 8 * slot, (uint32_t)((T / NSLOT) & 1));
+                ok = __all_sync(0xffffffffu, ok);               // the collective reads below
+                if (!ok) break;
+                tc_fence_after();
+                float a[COUT];
+                const uint32_t taddr = tmem + slot * NCOL + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-            for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, a + c0);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(acce0 + 8 * acc);
-            int vb, z;
-            const int q = tile_q0(t, vb, z) + r, y = q / PW, x = q - y * PW - 1;
-            if (y < v.h && x >= 0 && x < v.w) {
-                bf16 *yr = Y + ((((long long)vb * v.d + z) * v.h + y) * v.w + x) * COUT;
+                for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, a + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(acce0 + 8 * slot);
+                if (valid) {
+                    bf16 *yr = Y + ((((long long)U.b * v.d + U.z0 + i) * v.h + y) * v.w + x) * COUT;
 #pragma unroll
-                for (int c = 0; c < COUT; c += 8) {
-                    float o[8];
+                    for (int c = 0; c < COUT; c += 8) {
+                        float o[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        o[i] = a[c + i] + (bias ? __ldg(bias + c + i) : 0.f);
-                        if (relu) o[i] = fmaxf(o[i], 0.f);
+                        for (int e = 0; e < 8; ++e) {
+                            o[e] = a[c + e] + (bias ? __ldg(bias + c + e) : 0.f);
+                            if (relu) o[e] = fmaxf(o[e], 0.f);
+                        }
+                        uint4 pk;
+                        pk.x = pack_bf16(o[0], o[1]);
+                        pk.y = pack_bf16(o[2], o[3]);
+                        pk.z = pack_bf16(o[4], o[5]);
+                        pk.w = pack_bf16(o[6], o[7]);
+                        *reinterpret_cast<uint4 *>(yr + c) = pk;
                     }
-                    uint4 pk;
-                    pk.x = pack_bf16(o[0], o[1]);
-                    pk.y = pack_bf16(o[2], o[3]);
-                    pk.z = pack_bf16(o[4], o[5]);
-                    pk.w = pack_bf16(o[6], o[7]);
-                    *reinterpret_cast<uint4 *>(yr + c) = pk;
                 }
             }
         }
@@ -382,7 +397,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * NCOL) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NSLOT * NCOL) : "memory");
     }
 }
 
@@ -535,13 +550,28 @@ __global__ void bias_grad(const bf16 *dY, int npos, int c, float *db)
     if ((threadIdx.x & 31) == 0) atomicAdd(db + ch, s);
 }
 
-// input layer: the FP32 input as channel 0 of a 16-channel BF16 volume
-__global__ void pad_input(const float *x, int npos, bf16 *X16)
+// input layer: the FP32 input as channel 0 of a 16-channel BF16 volume, the n_aux medium
+// features (aux [volume][feature][position]) as channels 1 .. n_aux, zeros above
+__global__ void pad_input(const float *x, const float *aux, int n_aux, int vol, int npos, bf16 *X16)
 {
     GRID_LOOP(p, npos) {
         float f[8] = {x[p], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        st16(X16 + 16 * p, Bf8::from(f).u);
-        st16(X16 + 16 * p + 8, make_uint4(0u, 0u, 0u, 0u));
+        const int b = p / vol, q = p - b * vol;
+        for (int c = 0; c < n_aux; ++c) f[1 + c] = aux[((size_t)b * n_aux + c) * vol + q];
+        st16(X16 + 16 * (size_t)p, Bf8::from(f).u);
+        st16(X16 + 16 * (size_t)p + 8, make_uint4(0u, 0u, 0u, 0u));
+    }
+}
+
+// medium features of a label volume: log10(max(mua, 1e-4)) + 2 and
+// log10(max(mus (1 - g), 1e-3)), per voxel from a per-label table
+__global__ void features_kernel(const uint8_t *labels, int nvox, const float2 *tab, int n_media, float *out)
+{
+    GRID_LOOP(i, nvox) {
+        const int l = labels[i];
+        const float2 f = l < n_media ? tab[l] : make_float2(-2.f, -3.f);
+        out[i] = f.x;
+        out[(size_t)nvox + i] = f.y;
     }
 }
 
@@ -667,16 +697,25 @@ __global__ void head_bwd(const bf16 *Y, const float *out, const float *target, c
         st16(dY + 16 * (size_t)p, Bf8::from(g).u);
         st16(dY + 16 * (size_t)p + 8, Bf8::from(g + 8).u);
     }
+    // warp sums, then block sums in shared memory: 18 atomics per block
+    __shared__ float red[8][18];
     for (int o = 16; o > 0; o >>= 1) {
         l += __shfl_down_sync(0xffffffffu, l, o);
         gb += __shfl_down_sync(0xffffffffu, gb, o);
 #pragma unroll
         for (int c = 0; c < 16; ++c) gw[c] += __shfl_down_sync(0xffffffffu, gw[c], o);
     }
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(loss, l);
-        atomicAdd(dhb, gb);
-        for (int c = 0; c < 16; ++c) atomicAdd(dhw + c, gw[c]);
+        red[w][0] = l;
+        red[w][1] = gb;
+        for (int c = 0; c < 16; ++c) red[w][2 + c] = gw[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < 18) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k][threadIdx.x];
+        atomicAdd(threadIdx.x == 0 ? loss : threadIdx.x == 1 ? dhb : dhw + (threadIdx.x - 2), t);
     }
 }
 
@@ -811,11 +850,22 @@ cudaError_t launch_tc_t(const bf16 *X, const bf16 *W, const float *bias, Vol v, 
     if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
         return e;
     constexpr int ncol = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
-    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / (2 * ncol), 2048 / kTcThreads}));
-    const long long tiles = (long long)v.n * v.d * ((v.h * (v.w + 2) + kTcRows - 1) / kTcRows);
-    if (tiles * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
-    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(tiles, (long long)sms * per_sm));
-    conv3d_fwd_tc<CIN, COUT><<<blocks, kTcThreads, smem, st>>>(mx, mw, bias, v, relu, Y, err, ns);
+    constexpr int nslot = tc_wall(CIN, COUT) ? 4 : 2;
+    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / (nslot * ncol), 2048 / kTcThreads}));
+    const long long tiles_plane = (v.h * (v.w + 2) + kTcRows - 1) / kTcRows;
+    if ((long long)v.n * v.d * tiles_plane * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
+    // column depth: the deepest of 16, 8, 4, 2 that still leaves 3 units per resident CTA
+    // (a window then serves up to 3 tiles); on volumes too small for that, min(16, d);
+    // 1 without resident weights
+    int zc = 1;
+    if (tc_wall(CIN, COUT)) {
+        zc = std::min(16, v.d);
+        for (int z = 16; z >= 2; z /= 2)
+            if ((long long)v.n * ((v.d + z - 1) / z) * tiles_plane >= 3LL * sms * per_sm) { zc = z; break; }
+    }
+    const long long units = (long long)v.n * ((v.d + zc - 1) / zc) * tiles_plane;
+    const unsigned blocks = (unsigned)std::max<long long>(1, std::min<long long>(units, (long long)sms * per_sm));
+    conv3d_fwd_tc<CIN, COUT><<<blocks, kTcThreads, smem, st>>>(mx, mw, bias, v, relu, Y, err, ns, zc);
     return cudaGetLastError();
 }
 
@@ -871,7 +921,7 @@ thread_local std::string g_dn_err;
 }  // namespace
 
 struct mcx_denoiser {
-    int D, H, W, maxb;
+    int D, H, W, maxb, n_aux;
     size_t nparam = 0;
     std::vector<size_t> w_off, b_off;   // offsets of each layer's weights / bias in params
     size_t hw_off = 0, hb_off = 0;
@@ -931,11 +981,12 @@ static mcx_status refresh_weights(mcx_denoiser *d, cudaStream_t st)
 }
 
 // forward pass for n volumes; activations stay for the backward pass
-static mcx_status forward(mcx_denoiser *d, const float *x, int n, float *out, cudaStream_t st)
+static mcx_status forward(mcx_denoiser *d, const float *x, const float *aux, int n, float *out, cudaStream_t st)
 {
     const Vol v0 = level_vol(d, 0, n), v1 = level_vol(d, 1, n), v2 = level_vol(d, 2, n);
     const float *P = d->params.as<float>();
-    pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, (int)v0.pos(), d->x16.as<bf16>());
+    pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, aux, d->n_aux, d->D * d->H * d->W, (int)v0.pos(),
+                                              d->x16.as<bf16>());
     auto conv = [&](int l, const bf16 *in, Vol v) {
         return launch_fwd_tc(in, kLayers[l].cin, d->wf[l].as<bf16>(), P + d->b_off[l], v,
                              kLayers[l].cout, 1, d->a[l].as<bf16>(), d->status.as<unsigned>(), st);
@@ -983,7 +1034,7 @@ static mcx_status backward(mcx_denoiser *d, const float *x, const float *target,
     const float *P = d->params.as<float>();
     DNC(d, cudaMemsetAsync(d->grads.p, 0, d->nparam * sizeof(float), st), "clearing gradients");
     DNC(d, cudaMemsetAsync(d->loss.p, 0, sizeof(float), st), "clearing the loss");
-    head_bwd<<<grid1(v0.pos()), 256, 0, st>>>(d->a[9].as<bf16>(), d->out.as<float>(), target,
+    head_bwd<<<std::min(grid1(v0.pos()), 152u * 8u), 256, 0, st>>>(d->a[9].as<bf16>(), d->out.as<float>(), target,
                                              P + d->hw_off, (int)v0.pos(), d->ga[9].as<bf16>(),
                                              G + d->hw_off, G + d->hb_off, d->loss.as<float>());
     mcx_status s;
@@ -1012,18 +1063,19 @@ static mcx_status backward(mcx_denoiser *d, const float *x, const float *target,
 extern "C" {
 
 mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uint32_t nz,
-                               uint32_t max_batch, uint64_t seed)
+                               uint32_t max_batch, uint32_t n_aux, uint64_t seed)
 {
     if (!out) return dn_fail(nullptr, MCX_E_ARG, "out is NULL");
     *out = nullptr;
     if (nx % 64 || nx < 64 || nx > 252 || ny % 4 || nz % 4 || ny < 4 || nz < 4 || max_batch < 1)
         return dn_fail(nullptr, MCX_E_ARG,
                        "need nx a multiple of 64 up to 252, ny and nz multiples of 4, max_batch >= 1");
+    if (n_aux > 7) return dn_fail(nullptr, MCX_E_ARG, "n_aux must be 0..7");
     if ((unsigned long long)max_batch * nx * ny * nz * 96ull >= (1ull << 31))
         return dn_fail(nullptr, MCX_E_ARG, "max_batch * nx * ny * nz * 96 must stay below 2^31");
     mcx_denoiser *d = new (std::nothrow) mcx_denoiser();
     if (!d) return dn_fail(nullptr, MCX_E_OOM, "host allocation failed");
-    d->D = (int)nz; d->H = (int)ny; d->W = (int)nx; d->maxb = (int)max_batch;
+    d->D = (int)nz; d->H = (int)ny; d->W = (int)nx; d->maxb = (int)max_batch; d->n_aux = (int)n_aux;
     size_t off = 0;
     for (int l = 0; l < 10; ++l) {
         d->w_off.push_back(off);
@@ -1034,15 +1086,15 @@ mcx_status mcx_denoiser_create(mcx_denoiser **out, uint32_t nx, uint32_t ny, uin
     d->hw_off = off; off += 16;
     d->hb_off = off; off += 1;
     d->nparam = off;
-    // He-normal initial weights (fan-in 27 cin; the padded input layer's fan-in is 27)
+    // He-normal initial weights (fan-in 27 cin; the input layer's fan-in is 27 (1 + n_aux))
     std::vector<float> init(d->nparam, 0.f);
     std::mt19937_64 rng(seed);
     for (int l = 0; l < 10; ++l) {
-        const int fan = 27 * (l == 0 ? 1 : kLayers[l].cin);
+        const int fan = 27 * (l == 0 ? 1 + d->n_aux : kLayers[l].cin);
         std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / fan));
         for (size_t i = 0; i < 27ull * kLayers[l].cin * kLayers[l].cout; ++i) {
             const int ci = (int)(i % kLayers[l].cin);
-            init[d->w_off[l] + i] = (l == 0 && ci > 0) ? 0.f : (float)nd(rng);
+            init[d->w_off[l] + i] = (l == 0 && ci > d->n_aux) ? 0.f : (float)nd(rng);
         }
     }
     // the head starts at zero: the untrained network returns its input
@@ -1112,26 +1164,26 @@ mcx_status mcx_denoiser_set_params(mcx_denoiser *d, const float *host, uint64_t 
     return MCX_OK;
 }
 
-mcx_status mcx_denoiser_forward(mcx_denoiser *d, const float *x_dev, float *y_dev, uint32_t n,
-                                void *stream)
+mcx_status mcx_denoiser_forward(mcx_denoiser *d, const float *x_dev, const float *aux_dev, float *y_dev,
+                                uint32_t n, void *stream)
 {
-    if (!d || !x_dev || !y_dev) return dn_fail(d, MCX_E_ARG, "NULL argument");
+    if (!d || !x_dev || !y_dev || (d->n_aux && !aux_dev)) return dn_fail(d, MCX_E_ARG, "NULL argument");
     if (n < 1 || (int)n > d->maxb) return dn_fail(d, MCX_E_ARG, "n must be 1..max_batch");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    mcx_status s = forward(d, x_dev, (int)n, d->out.as<float>(), st);
+    mcx_status s = forward(d, x_dev, aux_dev, (int)n, d->out.as<float>(), st);
     if (s != MCX_OK) return s;
     DNC(d, cudaMemcpyAsync(y_dev, d->out.p, (size_t)level_vol(d, 0, n).pos() * 4, cudaMemcpyDeviceToDevice, st),
         "copying the output");
     return MCX_OK;
 }
 
-mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const float *t_dev,
-                                   uint32_t n, float lr, float *loss_host, void *stream)
+mcx_status mcx_denoiser_train_step(mcx_denoiser *d, const float *x_dev, const float *aux_dev,
+                                   const float *t_dev, uint32_t n, float lr, float *loss_host, void *stream)
 {
-    if (!d || !x_dev || !t_dev) return dn_fail(d, MCX_E_ARG, "NULL argument");
+    if (!d || !x_dev || !t_dev || (d->n_aux && !aux_dev)) return dn_fail(d, MCX_E_ARG, "NULL argument");
     if (n < 1 || (int)n > d->maxb) return dn_fail(d, MCX_E_ARG, "n must be 1..max_batch");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    mcx_status s = forward(d, x_dev, (int)n, d->out.as<float>(), st);
+    mcx_status s = forward(d, x_dev, aux_dev, (int)n, d->out.as<float>(), st);
     if (s != MCX_OK) return s;
     if ((s = backward(d, x_dev, t_dev, (int)n, st)) != MCX_OK) return s;
     if (lr > 0.f) {
@@ -1182,16 +1234,17 @@ mcx_status mcx_denoiser_decode(mcx_denoiser *d, const float *x_dev, float *phi_d
     return MCX_OK;
 }
 
-mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, float *phi_out_dev, uint32_t n,
-                              void *stream)
+mcx_status mcx_denoiser_apply(mcx_denoiser *d, const float *phi_in_dev, const float *aux_dev,
+                              float *phi_out_dev, uint32_t n, void *stream)
 {
-    if (!d || !phi_in_dev || !phi_out_dev) return dn_fail(d, MCX_E_ARG, "NULL argument");
+    if (!d || !phi_in_dev || !phi_out_dev || (d->n_aux && !aux_dev))
+        return dn_fail(d, MCX_E_ARG, "NULL argument");
     if (n < 1 || (int)n > d->maxb) return dn_fail(d, MCX_E_ARG, "n must be 1..max_batch");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long cnt = level_vol(d, 0, (int)n).pos();
     encode_kernel<<<grid1(cnt), 256, 0, st>>>(phi_in_dev, cnt, d->floor_, d->mu, 1.f / d->sigma, d->xin.as<float>());
     DNC(d, cudaGetLastError(), "encode");
-    mcx_status s = forward(d, d->xin.as<float>(), (int)n, d->out.as<float>(), st);
+    mcx_status s = forward(d, d->xin.as<float>(), aux_dev, (int)n, d->out.as<float>(), st);
     if (s != MCX_OK) return s;
     decode_kernel<<<grid1(cnt), 256, 0, st>>>(d->out.as<float>(), cnt, d->floor_, d->mu, d->sigma, phi_out_dev);
     DNC(d, cudaGetLastError(), "decode");
@@ -1216,6 +1269,28 @@ mcx_status mcx_denoiser_gather(mcx_denoiser *d, const float *set_dev, uint64_t s
     gather_kernel<<<grid1(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         set_dev, L, (int)n, d->D, d->H, d->W, dst_dev);
     DNC(d, cudaGetLastError(), "gather");
+    return MCX_OK;
+}
+
+mcx_status mcx_denoiser_features(const uint8_t *labels_dev, uint64_t nvox, uint32_t n_media,
+                                 const float *props, float *out_dev, void *stream)
+{
+    if (!labels_dev || !props || !out_dev || n_media < 1 || n_media > 256 || nvox >= (1ull << 30))
+        return dn_fail(nullptr, MCX_E_ARG, "bad arguments");
+    float2 tab[256];
+    for (uint32_t l = 0; l < n_media; ++l) {
+        const float mua = props[4 * l], mus = props[4 * l + 1], g = props[4 * l + 2];
+        tab[l] = make_float2(std::log10(std::max(mua, 1e-4f)) + 2.f, std::log10(std::max(mus * (1.f - g), 1e-3f)));
+    }
+    DBuf dt;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DNC(nullptr, dt.alloc(n_media * sizeof(float2)), "allocating the feature table");
+    DNC(nullptr, cudaMemcpyAsync(dt.p, tab, n_media * sizeof(float2), cudaMemcpyHostToDevice, st), "copying the table");
+    if (nvox) {
+        features_kernel<<<grid1((long long)nvox), 256, 0, st>>>(labels_dev, (int)nvox, dt.as<float2>(), (int)n_media, out_dev);
+        DNC(nullptr, cudaGetLastError(), "features");
+    }
+    DNC(nullptr, cudaStreamSynchronize(st), "waiting for the features");
     return MCX_OK;
 }
 

@@ -78,6 +78,25 @@ def test_conv_forward_matches_oracle(g, cin, cout):
     assert np.array_equal(got, bf16(got))                 # outputs are BF16 values
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 16), (48, 16)])
+def test_conv_forward_large_ragged_columns(g, cin, cout):
+    """a volume large enough for multi-plane work units, with a depth (36) that leaves a
+    ragged last column"""
+    import torch
+    rng = np.random.default_rng(300 + cin)
+    x = bf16(rng.normal(size=(2, 36, 64, 64, cin)).astype(np.float32))
+    w = bf16(rng.normal(size=(27, cout, cin)) / np.sqrt(27 * cin))
+    b = rng.normal(size=cout).astype(np.float32)
+    got = g.mcx_debug_conv3d(0, x, w, b).astype(np.float64)
+    xt, wt = torch.tensor(x), torch.tensor(w)
+    ref = np.maximum(od.conv3d(xt, wt, torch.tensor(b, dtype=torch.float64)).numpy(), 0)
+    s_abs = od.conv3d(xt.abs(), wt.abs()).numpy() + np.abs(b)
+    bound = 2.0 ** -8 * np.abs(ref) + 1.01 * 27 * cin * 2.0 ** -22 * s_abs
+    err = np.abs(got - ref)
+    print(f"conv {cin}->{cout} on 2x36x64x64: max err/bound {np.max(err / bound):.2f}")
+    assert np.all(err <= bound)
+
+
 @pytest.mark.parametrize("cin,cout", FWD_PAIRS)
 def test_conv_weight_gradient_matches_oracle(g, cin, cout):
     import torch
@@ -100,26 +119,29 @@ def test_conv_weight_gradient_matches_oracle(g, cin, cout):
     assert rel < 1e-5
 
 
-def _net(g, shape, n, params):
-    d = g.Denoiser(shape, max_batch=n, seed=1)
+def _net(g, shape, n, params, n_aux=0):
+    d = g.Denoiser(shape, max_batch=n, seed=1, n_aux=n_aux)
     d.set_params(params)
     return d
 
 
-def test_network_forward_matches_oracle(g, torch_cuda):
+@pytest.mark.parametrize("n_aux", [0, 2])
+def test_network_forward_matches_oracle(g, torch_cuda, n_aux):
     torch = torch_cuda
     rng = np.random.default_rng(11)
     shape, n = (8, 8, 64), 2
     p = random_params(rng)
     x = rng.normal(size=(n,) + shape).astype(np.float32)
-    with _net(g, shape, n, p) as d:
+    aux = rng.normal(size=(n, n_aux) + shape).astype(np.float32) if n_aux else None
+    with _net(g, shape, n, p, n_aux) as d:
         xd = torch.tensor(x, device="cuda")
         yd = torch.empty_like(xd)
-        d.forward(xd, yd)
+        d.forward(xd, yd, aux=None if aux is None else torch.tensor(aux, device="cuda"))
         d.sync()
         y = yd.cpu().numpy().astype(np.float64)
-    ref = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=True).numpy()
-    exact = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=False).numpy()
+    a64 = None if aux is None else aux.astype(np.float64)
+    ref = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=True, aux=a64).numpy()
+    exact = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=False, aux=a64).numpy()
     res_g, res_o = y - x, ref - x                 # the network's own contribution
     rel = np.linalg.norm(res_g - res_o) / np.linalg.norm(res_o)
     rel_exact = np.linalg.norm(exact - ref) / np.linalg.norm(res_o)
@@ -136,11 +158,14 @@ def test_network_gradients_match_oracle(g, torch_cuda):
     p = random_params(rng)
     x = rng.normal(size=(n,) + shape).astype(np.float32)
     t = (x + 0.3 * rng.normal(size=x.shape)).astype(np.float32)
-    with _net(g, shape, n, p) as d:
-        loss = d.train_step(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"), 0.0)
+    aux = rng.normal(size=(n, 2) + shape).astype(np.float32)
+    with _net(g, shape, n, p, n_aux=2) as d:
+        loss = d.train_step(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"), 0.0,
+                            aux=torch.tensor(aux, device="cuda"))
         gg = d.grads().astype(np.float64)
         assert np.array_equal(d.params(), p)      # lr = 0: no update
-    lo, go = od.loss_and_grads(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16=True)
+    lo, go = od.loss_and_grads(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16=True,
+                               aux=aux.astype(np.float64))
     print(f"loss gpu {loss:.6f} oracle {lo:.6f}")
     assert loss == pytest.approx(lo, rel=1e-4)
     k = 0
@@ -182,13 +207,14 @@ def test_apply_is_encode_forward_decode(g, torch_cuda):
     p = random_params(rng)
     phi = (10.0 ** rng.uniform(-9, 0, size=(n,) + shape)).astype(np.float32)
     phi[0, 0, 0, :5] = 0.0
-    with _net(g, shape, n, p) as d:
+    aux = torch.tensor(rng.normal(size=(n, 2) + shape).astype(np.float32), device="cuda")
+    with _net(g, shape, n, p, n_aux=2) as d:
         pd = torch.tensor(phi, device="cuda")
         out = torch.empty_like(pd)
-        d.apply(pd, out)
+        d.apply(pd, out, aux=aux)
         x, y, back = torch.empty_like(pd), torch.empty_like(pd), torch.empty_like(pd)
         d.encode(pd, x)
-        d.forward(x, y)
+        d.forward(x, y, aux=aux)
         d.decode(y, back)
         torch.cuda.synchronize()
         assert torch.equal(out, back)
@@ -240,6 +266,28 @@ def test_rejects_bad_shapes(g, torch_cuda):
             d.forward(x, torch.empty_like(x))
         with pytest.raises(ValueError):
             d.set_params(np.zeros(3, np.float32))
+    with g.Denoiser((4, 4, 64), max_batch=1, n_aux=2) as d:
+        x = torch.zeros((1, 4, 4, 64), device="cuda")
+        with pytest.raises(ValueError):
+            d.forward(x, torch.empty_like(x))              # the features are missing
+    with pytest.raises(g.McxError):
+        g.Denoiser((4, 4, 64), n_aux=8)
+
+
+def test_features_match_oracle(g, torch_cuda):
+    import workloads
+    torch = torch_cuda
+    wl = workloads.c5(1, seed=99)[0]
+    lab = torch.tensor(wl.labels, device="cuda")
+    out = torch.empty((2,) + wl.labels.shape, device="cuda")
+    g.Denoiser.features(lab, wl.media, out)
+    ref = od.features(wl.labels, np.asarray(wl.media, dtype=np.float32))
+    assert np.allclose(out.cpu().numpy(), ref, rtol=0, atol=2e-6)
+    # labels past the table count as exterior
+    lab2 = torch.tensor(np.array([0, 1, 9], dtype=np.uint8), device="cuda")
+    out2 = torch.empty(6, device="cuda")
+    g.Denoiser.features(lab2, wl.media[:2], out2)
+    assert np.allclose(out2.cpu().numpy().reshape(2, 3)[:, 2], [-2.0, -3.0])
 
 
 def test_gather_mirrors_and_transposes(g, torch_cuda):

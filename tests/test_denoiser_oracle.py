@@ -116,6 +116,36 @@ def test_first_layer_against_brute_force():
     assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
+def test_feature_channels_enter_the_first_layer():
+    """with features, channels 1..k of the input layer carry them (brute force)"""
+    rng = np.random.default_rng(17)
+    p = od.unpack(_random_params(rng))
+    x = rng.normal(size=(1, 2, 3, 4))
+    aux = rng.normal(size=(1, 2, 2, 3, 4))
+    x16 = np.zeros(x.shape + (16,))
+    x16[..., 0] = x
+    x16[..., 1] = aux[:, 0]
+    x16[..., 2] = aux[:, 1]
+    ref = np.maximum(_brute_conv(x16, p["e1a.w"].numpy(), p["e1a.b"].numpy()), 0)
+    got = torch.relu(od.conv3d(torch.tensor(x16), p["e1a.w"], p["e1a.b"])).numpy()
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)
+    # and the network sees them: changing a feature changes the output
+    pp = _random_params(rng)
+    xv = rng.normal(size=(1, 4, 4, 4))
+    av = rng.normal(size=(1, 2, 4, 4, 4))
+    y0 = od.forward(pp, xv, bf16=False, aux=av).numpy()
+    av[0, 1, 1, 1, 1] += 1.0
+    assert not np.allclose(od.forward(pp, xv, bf16=False, aux=av).numpy(), y0)
+
+
+def test_features_values():
+    media = np.array([(0.0, 0.0, 1.0, 1.0), (0.01, 10.0, 0.9, 1.37), (0.1, 5.0, 0.5, 1.4)])
+    labels = np.array([0, 1, 2, 7], dtype=np.uint8)
+    f = od.features(labels, media)
+    assert np.allclose(f[0], [np.log10(1e-4) + 2, 0.0, 1.0, -2.0])
+    assert np.allclose(f[1], [-3.0, 0.0, np.log10(2.5), -3.0])
+
+
 def test_forward_equivariant_under_shifts_of_four():
     """pooling twice makes the network equivariant under shifts by multiples of 4 voxels,
     up to the receptive field's reach of the zero-padded boundary"""
@@ -135,7 +165,8 @@ def test_gradients_against_finite_differences():
     p = _random_params(rng)
     x = rng.normal(size=(1, 4, 4, 8))
     t = x + 0.3 * rng.normal(size=x.shape)
-    loss, g = od.loss_and_grads(p, x, t, bf16=False)
+    aux = rng.normal(size=(1, 2) + x.shape[1:])
+    loss, g = od.loss_and_grads(p, x, t, bf16=False, aux=aux)
     # parameters in every layer, the biases and the head
     idx = []
     k = 0
@@ -148,8 +179,8 @@ def test_gradients_against_finite_differences():
         pp, pm = p.copy(), p.copy()
         pp[i] += h
         pm[i] -= h
-        lp = float(((od.forward(pp, x, bf16=False) - torch.tensor(t)) ** 2).mean())
-        lm = float(((od.forward(pm, x, bf16=False) - torch.tensor(t)) ** 2).mean())
+        lp = float(((od.forward(pp, x, bf16=False, aux=aux) - torch.tensor(t)) ** 2).mean())
+        lm = float(((od.forward(pm, x, bf16=False, aux=aux) - torch.tensor(t)) ** 2).mean())
         fd = (lp - lm) / (2 * h)
         assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9), i
 
