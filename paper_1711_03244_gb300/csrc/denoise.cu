@@ -147,11 +147,14 @@ __host__ __device__ constexpr int tc_smem_bytes(int cin, int cout, int w, int ns
 {
     return 1024 + kTcHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + ns * tc_stage_bytes(cin, cout, w);
 }
-// ring depth: 4-8 stages within kTcSmemBudget (two or more CTAs per SM), else 2-4 stages
-// within one SM's shared memory; 0 when not even 2 fit
+// ring depth: each CTA has one MMA-issuing thread, so more resident CTAs issue more
+// MMAs; prefer 3-8 stages within a quarter of the SM's shared memory (4 CTAs), then 2-8
+// within half (2 CTAs), then 2-4 within all of it; 0 when not even 2 fit
 __host__ __device__ constexpr int tc_stages(int cin, int cout, int w)
 {
-    for (int ns = kTcMaxStages; ns >= 4; --ns)
+    for (int ns = kTcMaxStages; ns >= 3; --ns)
+        if (tc_smem_bytes(cin, cout, w, ns) <= kTcSmemBudget / 2) return ns;
+    for (int ns = kTcMaxStages; ns >= 2; --ns)
         if (tc_smem_bytes(cin, cout, w, ns) <= kTcSmemBudget) return ns;
     for (int ns = 4; ns >= 2; --ns)
         if (tc_smem_bytes(cin, cout, w, ns) <= kTcSmemMax) return ns;
