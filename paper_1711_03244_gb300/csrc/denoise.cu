@@ -404,71 +404,191 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     }
 }
 
-// Weight gradient of one tap: dW[tap][co][ci] += sum_p dY[p][co] * X[p + off(tap)][ci],
-// a GEMM with M = Cout (16 per warp), N = Cin (8 per mma), K = positions (16 per mma),
-// over one chunk of positions; chunks are summed with FP32 atomics.
-template <int CIN>
-__global__ void __launch_bounds__(128)
-conv3d_bwd_w(const bf16 *__restrict__ X, const bf16 *__restrict__ dY, int cout, Vol v,
-             long long chunk, float *__restrict__ dW)
+// Weight gradient: dW[tap][co][ci] = sum_p dY[p][co] X[p + off(tap)][ci], over the same
+// tiles and windows as the forward kernel (positions q along padded lines; the dY tile's
+// pad rows come in as zeros from the tensor map, so the windows' pad and neighbour rows
+// contribute nothing).  The GEMM per tap has M = cout (16 per fragment), N = cin (8 per
+// fragment) and K = the tile's 128 positions: too narrow in M for tcgen05 (M >= 64), so it
+// runs on warp-level mma.sync m16n8k16 with operands read from shared memory by
+// ldmatrix.trans (the staged rows are position-major, the fragments want the position
+// index along K).  One producer thread streams (dY tile, X window) stages by TMA; eight
+// consumer warps each own a fixed share of the (tap, m-fragment, n-fragment pair) units
+// and accumulate them in registers over every tile the CTA handles, then add them to dW
+// with FP32 atomics.  With many units per warp the taps are split over three CTA groups
+// (one per dz); each stage then carries only that plane's window.
+constexpr int kWgConsumers = 8, kWgThreads = 32 * (kWgConsumers + 1);
+
+__host__ __device__ constexpr int wg_units_per_warp(int cin, int cout)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    const int tap = blockIdx.y;
-    const int mt = warp;                                   // rows co = 16 mt .. 16 mt + 15
-    if (mt * 16 >= cout) return;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long P = v.pos();
-    const long long pbeg = blockIdx.x * chunk, pend = min(P, pbeg + chunk);
-    float acc[CIN / 8][4];
-#pragma unroll
-    for (int j = 0; j < CIN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    const int co_a = mt * 16 + g, co_b = co_a + 8;
-    for (long long k0 = pbeg; k0 < pend; k0 += 16) {
-        // four positions per thread: k0 + 2t, +1, +8, +9
-        long long pk[4] = {k0 + 2 * t, k0 + 2 * t + 1, k0 + 2 * t + 8, k0 + 2 * t + 9};
-        float ya[4], yb[4];
-        long long src[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const long long p = pk[i];
-            bool ok = p < pend;
-            long long s = -1;
-            if (ok) {
-                const int x = (int)(p % v.w);
-                long long r = p / v.w;
-                const int yy = (int)(r % v.h);
-                r /= v.h;
-                const int zz = (int)(r % v.d);
-                const int bb = (int)(r / v.d);
-                const int xs = x + dx, ys = yy + dy, zs = zz + dz;
-                if (xs >= 0 && xs < v.w && ys >= 0 && ys < v.h && zs >= 0 && zs < v.d)
-                    s = (((long long)bb * v.d + zs) * v.h + ys) * v.w + xs;
+    return (9 * (cout / 16) * (cin / 16) + kWgConsumers - 1) / kWgConsumers;
+}
+// dz groups over CTAs: 1 (a CTA handles all 27 taps) when its accumulators fit in 96
+// registers, else 3
+__host__ __device__ constexpr int wg_groups(int cin, int cout) { return 3 * wg_units_per_warp(cin, cout) * 8 <= 96 ? 1 : 3; }
+__host__ __device__ constexpr int wg_dy_lines(int w) { return (127 + w + 1) / (w + 2) + 1; }
+__host__ __device__ constexpr int wg_lbo_dy(int w) { return ((wg_dy_lines(w) * (w + 2) * 16 + 127) / 128) * 128; }
+__host__ __device__ constexpr int wg_stage_bytes(int cin, int cout, int w)
+{
+    return (cout / 8) * wg_lbo_dy(w) + (cin / 8) * tc_lbo_a(w);
+}
+__host__ __device__ constexpr int wg_smem_bytes(int cin, int cout, int w, int ns)
+{
+    return 1024 + kTcHeader + ns * wg_stage_bytes(cin, cout, w);
+}
+__host__ __device__ constexpr int wg_stages(int cin, int cout, int w)
+{
+    for (int ns = 6; ns >= 3; --ns)
+        if (wg_smem_bytes(cin, cout, w, ns) <= kTcSmemBudget) return ns;
+    for (int ns = 4; ns >= 2; --ns)
+        if (wg_smem_bytes(cin, cout, w, ns) <= kTcSmemMax) return ns;
+    return 0;
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr) : "memory");
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kWgThreads)
+conv3d_wgrad(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy, Vol v, int ns,
+             float *__restrict__ dW, unsigned *err)
+{
+    constexpr int MT = COUT / 16, NP = CIN / 16, U = 9 * MT * NP, UPW = wg_units_per_warp(CIN, COUT);
+    constexpr int G = wg_groups(CIN, COUT), DZN = 3 / G;          // planes (dz) per CTA
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t full0 = base, empty0 = base + 64;
+    const int PW = v.w + 2, Lx = tc_lines(v.w), Ly = wg_dy_lines(v.w);
+    const int lbo_x = tc_lbo_a(v.w), lbo_y = wg_lbo_dy(v.w);
+    const int y_bytes = (COUT / 8) * lbo_y, stage_bytes = wg_stage_bytes(CIN, COUT, v.w);
+    const uint32_t ring = base + kTcHeader;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int dz0 = G == 1 ? 0 : (int)blockIdx.y;                  // first plane index (0..2)
+    const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
+    const int n_tiles = v.n * v.d * tiles_plane;
+    const int my_tiles = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_steps = my_tiles * DZN;
+    struct Tl { int b, z, q0; };
+    auto tile_of = [&](int t) {
+        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+        const int plane = tile / tiles_plane;
+        return Tl{plane / v.d, plane % v.d, (tile % tiles_plane) * kTcRows};
+    };
+    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
+
+    if (tid == 0) {
+        for (int b = 0; b < ns; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, kWgConsumers);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = true;
+
+    if (warp == kWgConsumers) {
+        // ------------------------------------------------------------ producer (TMA)
+        if (lane == 0) {
+            const uint32_t tx = (COUT / 8) * (Ly * PW * 16) + (CIN / 8) * (Lx * PW * 16);
+            int b = 0, use = 0;
+            for (int s = 0; s < n_steps && ok; ++s) {
+                if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
+                if (!ok) break;
+                const Tl T = tile_of(s / DZN);
+                const int dz = dz0 + s % DZN - 1;
+                const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
+                mbar_expect_tx(fb, tx);
+                for (int c = 0; c < COUT / 8; ++c)
+                    tma_load_5d(st + c * lbo_y, &tmdy, 8 * c, -1, T.q0 / PW, T.z, T.b, fb);
+                for (int c = 0; c < CIN / 8; ++c)
+                    tma_load_5d(st + y_bytes + c * lbo_x, &tmx, 8 * c, -1, first_line(T.q0), T.z + dz, T.b, fb);
+                if (++b == ns) { b = 0; ++use; }
             }
-            src[i] = s;
-            ya[i] = ok ? __bfloat162float(dY[p * cout + co_a]) : 0.f;
-            yb[i] = ok ? __bfloat162float(dY[p * cout + co_b]) : 0.f;
+            for (int bb = 0; bb < ns; ++bb) {                 // every load has landed
+                const int issued = use + (bb < b ? 1 : 0);
+                if (issued > 0) ok &= mbar_wait(full0 + 8 * bb, (uint32_t)((issued - 1) & 1));
+            }
         }
-        const unsigned a0 = pack_bf16(ya[0], ya[1]), a1 = pack_bf16(yb[0], yb[1]);
-        const unsigned a2 = pack_bf16(ya[2], ya[3]), a3 = pack_bf16(yb[2], yb[3]);
+    } else {
+        // ------------------------------------------------------------ consumers (mma.sync)
+        float acc[DZN][UPW][2][4];
 #pragma unroll
-        for (int j = 0; j < CIN / 8; ++j) {
-            const int ci = j * 8 + g;
-            float xv[4];
+        for (int a = 0; a < DZN; ++a)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = src[i] >= 0 ? __bfloat162float(X[src[i] * CIN + ci]) : 0.f;
-            mma_bf16(acc[j], a0, a1, a2, a3, pack_bf16(xv[0], xv[1]), pack_bf16(xv[2], xv[3]));
+            for (int u = 0; u < UPW; ++u)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) acc[a][u][h][0] = acc[a][u][h][1] = acc[a][u][h][2] = acc[a][u][h][3] = 0.f;
+        // ldmatrix row addresses: lane l serves row l % 8 of matrix l / 8
+        const int mrow = (lane & 7) + ((lane >> 4) << 3);      // + 8 for matrices 2, 3 (A)
+        const int mcol = (lane >> 3) & 1;                      // chunk + 1 for matrices 1, 3 (A)
+        const int brow = (lane & 7) + (((lane >> 3) & 1) << 3); // + 8 for matrices 1, 3 (B)
+        const int bcol = lane >> 4;                            // chunk + 1 for matrices 2, 3 (B)
+        int b = 0, use = 0;
+        for (int s = 0; s < n_steps && ok; ++s) {
+            ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const Tl T = tile_of(s / DZN);
+            const int dzl = s % DZN;
+            const uint32_t Ys = ring + b * stage_bytes, Xs = Ys + y_bytes;
+            const int offy = T.q0 - (T.q0 / PW) * PW, offx = T.q0 - first_line(T.q0) * PW;
+#pragma unroll
+            for (int dzc = 0; dzc < DZN; ++dzc) {
+                if (dzc != dzl) continue;                      // registers indexed statically
+#pragma unroll 1
+                for (int ks = 0; ks < 8; ++ks) {
+                    unsigned af[MT][4];
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+                        ldsm_x4_t(Ys + (2 * mt + mcol) * lbo_y + (offy + 16 * ks + mrow) * 16,
+                                  af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
+#pragma unroll
+                    for (int j = 0; j < UPW; ++j) {
+                        const int u = warp + kWgConsumers * j;
+                        if (u >= U) break;
+                        const int t9 = u / (MT * NP), mt = (u / NP) % MT, np = u % NP;
+                        unsigned b0, b1, b2, b3;
+                        const int toff = (t9 / 3 - 1) * PW + (t9 % 3 - 1);   // (dy, dx) row shift
+                        ldsm_x4_t(Xs + (2 * np + bcol) * lbo_x + (offx + toff + 16 * ks + brow) * 16, b0, b1, b2, b3);
+                        unsigned a0 = af[0][0], a1 = af[0][1], a2 = af[0][2], a3 = af[0][3];
+#pragma unroll
+                        for (int m = 1; m < MT; ++m)
+                            if (m == mt) { a0 = af[m][0]; a1 = af[m][1]; a2 = af[m][2]; a3 = af[m][3]; }
+                        mma_bf16(acc[dzc][j][0], a0, a1, a2, a3, b0, b1);
+                        mma_bf16(acc[dzc][j][1], a0, a1, a2, a3, b2, b3);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * b);
+            if (++b == ns) { b = 0; ++use; }
+        }
+        // add this CTA's sums to dW[tap][co][ci]
+        if (ok && my_tiles) {
+            const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+            for (int dzc = 0; dzc < DZN; ++dzc)
+#pragma unroll
+                for (int j = 0; j < UPW; ++j) {
+                    const int u = warp + kWgConsumers * j;
+                    if (u >= U) break;
+                    const int t9 = u / (MT * NP), mt = (u / NP) % MT, np = u % NP;
+                    const int tap = 9 * (dz0 + dzc) + t9;
+                    float *w = dW + (size_t)tap * COUT * CIN;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int ci = 16 * np + 8 * h + 2 * t, co = 16 * mt + g;
+                        atomicAdd(w + (size_t)co * CIN + ci, acc[dzc][j][h][0]);
+                        atomicAdd(w + (size_t)co * CIN + ci + 1, acc[dzc][j][h][1]);
+                        atomicAdd(w + (size_t)(co + 8) * CIN + ci, acc[dzc][j][h][2]);
+                        atomicAdd(w + (size_t)(co + 8) * CIN + ci + 1, acc[dzc][j][h][3]);
+                    }
+                }
         }
     }
-    float *dWt = dW + (size_t)tap * cout * CIN;
-#pragma unroll
-    for (int j = 0; j < CIN / 8; ++j) {
-        const int ci = j * 8 + 2 * t;
-        atomicAdd(dWt + (size_t)co_a * CIN + ci, acc[j][0]);
-        atomicAdd(dWt + (size_t)co_a * CIN + ci + 1, acc[j][1]);
-        atomicAdd(dWt + (size_t)co_b * CIN + ci, acc[j][2]);
-        atomicAdd(dWt + (size_t)co_b * CIN + ci + 1, acc[j][3]);
-    }
+    if (!__syncthreads_and(ok) && tid == 0) atomicOr(err, 1u);
 }
 
 // ------------------------------------------------------------------------ elementwise
@@ -884,22 +1004,55 @@ cudaError_t launch_fwd_tc(const bf16 *X, int cin, const bf16 *W, const float *bi
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_bwd_w(const bf16 *X, int cin, const bf16 *dY, int cout, Vol v, float *dW,
+template <int CIN, int COUT>
+cudaError_t launch_wg_t(const bf16 *X, const bf16 *dY, Vol v, float *dW, unsigned *err, cudaStream_t st)
+{
+    if (v.w + 2 > 256 || tc_lines(v.w) > 256) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap mx, my;
+    const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+    auto map5 = [&](CUtensorMap *m, const bf16 *ptr, int c, int lines) {
+        const cuuint64_t dim[5] = {(cuuint64_t)c, (cuuint64_t)v.w, (cuuint64_t)v.h, (cuuint64_t)v.d, (cuuint64_t)v.n};
+        const cuuint64_t str[4] = {(cuuint64_t)c * 2, (cuuint64_t)v.w * c * 2, (cuuint64_t)v.h * v.w * c * 2,
+                                   (cuuint64_t)v.d * v.h * v.w * c * 2};
+        const cuuint32_t box[5] = {8, (cuuint32_t)(v.w + 2), (cuuint32_t)lines, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(ptr), dim, str, box, one,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    if (!map5(&mx, X, CIN, tc_lines(v.w)) || !map5(&my, dY, COUT, wg_dy_lines(v.w))) return cudaErrorInvalidValue;
+    const int ns = wg_stages(CIN, COUT, v.w);
+    if (ns < 2) return cudaErrorInvalidValue;
+    const int smem = wg_smem_bytes(CIN, COUT, v.w, ns);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, smem_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    constexpr int G = wg_groups(CIN, COUT);
+    const int per_sm = std::max(1, std::min(smem_sm / (smem + 1024), 2048 / kWgThreads));
+    const long long tiles = (long long)v.n * v.d * ((v.h * (v.w + 2) + kTcRows - 1) / kTcRows);
+    if (tiles * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
+    // CTAs per group: every resident slot, but at least 4 tiles each (the final atomics)
+    const long long per_group = std::max<long long>(1, std::min<long long>((tiles + 3) / 4, (long long)sms * per_sm / G));
+    const dim3 grid((unsigned)per_group, G);
+    conv3d_wgrad<CIN, COUT><<<grid, kWgThreads, smem, st>>>(mx, my, v, ns, dW, err);
+    return cudaGetLastError();
+}
+
+// dW (FP32, [27][cout][cin]) += the weight gradient of a convolution with input X and
+// output gradient dY; (cin, cout) one of the network's layer pairs
+cudaError_t launch_bwd_w(const bf16 *X, int cin, const bf16 *dY, int cout, Vol v, float *dW, unsigned *err,
                          cudaStream_t st)
 {
-    // about 48 position chunks per tap: enough blocks to fill the GPU, few FP32 atomics
-    const long long chunk = std::max<long long>(2048, ((v.pos() / 48 + 15) / 16) * 16);
-    const dim3 grid((unsigned)((v.pos() + chunk - 1) / chunk), 27);
-    const int warps = (cout + 15) / 16;
-    switch (cin) {
-    case 16: conv3d_bwd_w<16><<<grid, 32 * warps, 0, st>>>(X, dY, cout, v, chunk, dW); break;
-    case 32: conv3d_bwd_w<32><<<grid, 32 * warps, 0, st>>>(X, dY, cout, v, chunk, dW); break;
-    case 48: conv3d_bwd_w<48><<<grid, 32 * warps, 0, st>>>(X, dY, cout, v, chunk, dW); break;
-    case 64: conv3d_bwd_w<64><<<grid, 32 * warps, 0, st>>>(X, dY, cout, v, chunk, dW); break;
-    case 96: conv3d_bwd_w<96><<<grid, 32 * warps, 0, st>>>(X, dY, cout, v, chunk, dW); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+#define MCX_WG(ci, co) \
+    if (cin == ci && cout == co) return launch_wg_t<ci, co>(X, dY, v, dW, err, st);
+    MCX_WG(16, 16) MCX_WG(16, 32) MCX_WG(32, 32) MCX_WG(32, 64) MCX_WG(64, 64) MCX_WG(96, 32) MCX_WG(48, 16)
+#undef MCX_WG
+    return cudaErrorInvalidValue;
 }
 
 struct DBuf {
@@ -1023,7 +1176,7 @@ static mcx_status conv_bwd(mcx_denoiser *d, int l, const bf16 *in, Vol v, bf16 *
     bf16 *dA = d->ga[l].as<bf16>();
     relu_mask<<<grid1(v.pos() * L.cout / 8), 256, 0, st>>>(dA, d->a[l].as<bf16>(), (int)(v.pos() * L.cout / 8));
     bias_grad<<<dim3(64, L.cout), 256, 0, st>>>(dA, (int)v.pos(), L.cout, G + d->b_off[l]);
-    DNC(d, launch_bwd_w(in, L.cin, dA, L.cout, v, G + d->w_off[l], st), "weight gradient");
+    DNC(d, launch_bwd_w(in, L.cin, dA, L.cout, v, G + d->w_off[l], d->status.as<unsigned>(), st), "weight gradient");
     if (dIn)
         DNC(d, launch_fwd_tc(dA, L.cout, d->wb[l].as<bf16>(), nullptr, v, L.cin, 0, dIn, d->status.as<unsigned>(), st),
             "input gradient");
@@ -1354,7 +1507,14 @@ mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t dd, int32_t hh, int
         if (e == cudaSuccess) e = cudaMemcpy(bdy.p, hdy.data(), hdy.size() * 2, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = bdw.alloc(27ull * cin * cout * 4);
         if (e == cudaSuccess) e = cudaMemset(bdw.p, 0, 27ull * cin * cout * 4);
-        if (e == cudaSuccess) e = launch_bwd_w(bx.as<bf16>(), cin, bdy.as<bf16>(), cout, v, bdw.as<float>(), nullptr);
+        DBuf berr;
+        if (e == cudaSuccess) e = berr.alloc(4);
+        if (e == cudaSuccess) e = cudaMemset(berr.p, 0, 4);
+        if (e == cudaSuccess)
+            e = launch_bwd_w(bx.as<bf16>(), cin, bdy.as<bf16>(), cout, v, bdw.as<float>(), berr.as<unsigned>(), nullptr);
+        unsigned herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, berr.p, 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && herr) return dn_fail(nullptr, MCX_E_TIMEOUT, "weight-gradient wait timed out");
         if (e == cudaSuccess) e = cudaMemcpy(out, bdw.p, 27ull * cin * cout * 4, cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) return dn_fail(nullptr, MCX_E_CUDA, std::string("debug conv: ") + cudaGetErrorString(e));
