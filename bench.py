@@ -279,7 +279,10 @@ def study_denoise(args):
     target: args.dn_target photons, independent seeds), then on held-out volumes compare
     the voxel-wise log10 RMS error against args.dn_ref-photon references of the denoised
     low-photon map with plain runs along a photon ladder, and the wall time (walk kernel
-    time, plus the network pass for the denoised path) at equal error."""
+    time, plus the network pass for the denoised path) at equal error.  Every training
+    configuration of args.dn_configs ("steps:batch:lr", comma separated) is trained from
+    the same initial weights on the same data and evaluated on the same held-out runs;
+    one JSON line each."""
     import torch
     import paper_1711_03244_gb300 as mcx
     from paper_1711_03244_gb300 import build as mcx_build
@@ -288,36 +291,34 @@ def study_denoise(args):
     mcx.load()
     dev = torch.device("cuda")
     shape = (64, 64, 64)
+    n_aux = args.dn_aux
+    configs = [tuple(c.split(":")) for c in args.dn_configs.split(",")] if args.dn_configs else \
+        [(str(args.dn_steps), str(args.dn_batch), str(args.dn_lr))]
+    configs = [(int(a), int(b), float(c)) for a, b, c in configs]
     train_v = workloads.c5(args.dn_train, seed=1711032450)
     test_v = workloads.c5(args.dn_test, seed=1711032451)
+    n_t = len(test_v)
+
+    # training data: network-domain pairs (a throw-away denoiser object does the encoding)
     t0 = time.time()
     phi_in = torch.empty((len(train_v),) + shape, device=dev)
     phi_tg = torch.empty_like(phi_in)
     ms_in = dn.simulate(train_v, args.dn_in, phi_in, seed_offset=0)
     ms_tg = dn.simulate(train_v, args.dn_target, phi_tg, seed_offset=1_000_003)
     gen_s = time.time() - t0
-    maxb = max(args.dn_batch, 16)
-    n_aux = args.dn_aux
-    d = mcx.Denoiser(shape, max_batch=maxb, seed=args.dn_seed, n_aux=n_aux)
-    x_set, t_set = torch.empty_like(phi_in), torch.empty_like(phi_tg)
-    dn.encode_set(d, phi_in, x_set)
-    dn.encode_set(d, phi_tg, t_set)
+    with mcx.Denoiser(shape, max_batch=1) as enc:
+        x_set, t_set = torch.empty_like(phi_in), torch.empty_like(phi_tg)
+        dn.encode_set(enc, phi_in, x_set)
+        dn.encode_set(enc, phi_tg, t_set)
     del phi_in, phi_tg
-    aux_set = None
+    aux_set = aux_t = None
     if n_aux:
         aux_set = torch.empty((len(train_v), 2) + shape, device=dev)
         dn.features(train_v, aux_set)
-    torch.cuda.synchronize()
-    t1 = time.time()
-    losses = dn.train(d, x_set, t_set, args.dn_steps, args.dn_batch, lr=args.dn_lr,
-                      lr_final=args.dn_lr / 10, seed=args.dn_seed, log_every=max(args.dn_steps // 10, 1),
-                      aux_set=aux_set)
-    torch.cuda.synchronize()
-    train_s = time.time() - t1
-    del x_set, t_set, aux_set
+        aux_t = torch.empty((n_t, 2) + shape, device=dev)
+        dn.features(test_v, aux_t)
 
-    # held-out evaluation
-    n_t = len(test_v)
+    # held-out references and the plain photon ladder
     ref = torch.empty((n_t,) + shape, device=dev)
     dn.simulate(test_v, args.dn_ref, ref, seed_offset=2_000_003)
     ref_h = ref.cpu().numpy()
@@ -325,70 +326,75 @@ def study_denoise(args):
     ladder = [n for n in ladder if n <= args.dn_ladder_max]
     plain_rms, plain_ms = [], []
     low = torch.empty_like(ref)
-    for k, n in enumerate(ladder):
-        ms = dn.simulate(test_v, n, low, seed_offset=3_000_017 + k)
+    for li, n in enumerate(ladder):
+        ms = dn.simulate(test_v, n, low, seed_offset=3_000_017 + li)
         h = low.cpu().numpy()
         plain_rms.append(float(np.mean([dn.log_rms(h[i], ref_h[i]) for i in range(n_t)])))
         plain_ms.append(ms)
-        if k == 0:
+        if li == 0:
             low_in = low.clone()
             walk_in_ms = ms
-    out = torch.empty_like(ref)
-    aux_t = None
-    if n_aux:
-        aux_t = torch.empty((n_t, 2) + shape, device=dev)
-        dn.features(test_v, aux_t)
-    dn.denoise(d, low_in, out, aux=aux_t)          # warm-up
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    e0.record()
-    for _ in range(reps):
-        dn.denoise(d, low_in, out, aux=aux_t)
-    e1.record()
-    e1.synchronize()
-    d.sync()
-    apply_ms = e0.elapsed_time(e1) / reps
-    oh = out.cpu().numpy()
-    den_rms = float(np.mean([dn.log_rms(oh[i], ref_h[i]) for i in range(n_t)]))
-    # photons (and walk time) a plain run needs for the denoised error: log-log
-    # interpolation along the ladder, extrapolated with the last slope past its end
-    lr_, ln_ = np.log(plain_rms), np.log(ladder)
-    lt_ = np.log(plain_ms)
-    if den_rms >= plain_rms[0]:
-        n_eq, t_eq, how = float(ladder[0]), plain_ms[0], "denoised no better than the input"
-    else:
-        j = next((j for j in range(1, len(ladder)) if plain_rms[j] <= den_rms), None)
-        how = "interpolated"
-        if j is None:
-            j, how = len(ladder) - 1, "extrapolated"
-        a = (np.log(den_rms) - lr_[j - 1]) / (lr_[j] - lr_[j - 1])
-        n_eq = float(np.exp(ln_[j - 1] + a * (ln_[j] - ln_[j - 1])))
-        t_eq = float(np.exp(lt_[j - 1] + a * (lt_[j] - lt_[j - 1])))
-    den_ms = walk_in_ms + apply_ms
+    del low
+    lr_, ln_, lt_ = np.log(plain_rms), np.log(ladder), np.log(plain_ms)
     # tensor-core work of one forward pass per volume (the ten 3x3x3 convolutions)
     npos = [64 ** 3, 64 ** 3, 32 ** 3, 32 ** 3, 16 ** 3, 16 ** 3, 32 ** 3, 32 ** 3, 64 ** 3, 64 ** 3]
     chans = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
     fwd_flop = sum(2 * p * 27 * ci * co for p, (ci, co) in zip(npos, chans))
     pk = peaks()
-    tflops = fwd_flop * n_t / (apply_ms * 1e-3) / 1e12
-    print(json.dumps({
-        "study": "denoise", "volumes": "64x64x64 mm, 1-3 ellipsoids, random optics (c5)",
-        "feature_channels": n_aux,
-        "train_volumes": len(train_v), "test_volumes": n_t, "photons_input": args.dn_in,
-        "photons_target": args.dn_target, "photons_reference": args.dn_ref,
-        "data_walk_ms": ms_in + ms_tg, "data_wall_s": gen_s,
-        "train_steps": args.dn_steps, "train_batch": args.dn_batch, "train_s": train_s,
-        "train_ms_per_step": 1e3 * train_s / max(args.dn_steps, 1),
-        "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-50:])),
-        "ladder_photons": ladder, "ladder_rms": plain_rms, "ladder_walk_ms": plain_ms,
-        "input_rms": plain_rms[0], "denoised_rms": den_rms,
-        "plain_photons_for_denoised_rms": n_eq, "plain_ms_for_denoised_rms": t_eq, "equal_error": how,
-        "denoised_ms": den_ms, "denoised_walk_ms": walk_in_ms, "denoiser_apply_ms": apply_ms,
-        "time_fraction_of_plain": den_ms / t_eq if t_eq else None,
-        "apply_tflops": tflops, "bf16_peak_tflops": pk["bf16_tflops"],
-        "apply_frac_of_peak": tflops / pk["bf16_tflops"] if pk["bf16_tflops"] else None,
-    }), flush=True)
-    d.close()
+
+    for steps, batch, lr in configs:
+        d = mcx.Denoiser(shape, max_batch=max(batch, 16), seed=args.dn_seed, n_aux=n_aux)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        losses = dn.train(d, x_set, t_set, steps, batch, lr=lr, lr_final=lr / 10, seed=args.dn_seed,
+                          log_every=max(steps // 10, 1), aux_set=aux_set)
+        torch.cuda.synchronize()
+        train_s = time.time() - t1
+        out = torch.empty_like(ref)
+        dn.denoise(d, low_in, out, aux=aux_t)      # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            dn.denoise(d, low_in, out, aux=aux_t)
+        e1.record()
+        e1.synchronize()
+        d.sync()
+        apply_ms = e0.elapsed_time(e1) / reps
+        oh = out.cpu().numpy()
+        den_rms = float(np.mean([dn.log_rms(oh[i], ref_h[i]) for i in range(n_t)]))
+        # photons (and walk time) a plain run needs for the denoised error: log-log
+        # interpolation along the ladder, extrapolated with the last slope past its end
+        if den_rms >= plain_rms[0]:
+            n_eq, t_eq, how = float(ladder[0]), plain_ms[0], "denoised no better than the input"
+        else:
+            j = next((j for j in range(1, len(ladder)) if plain_rms[j] <= den_rms), None)
+            how = "interpolated"
+            if j is None:
+                j, how = len(ladder) - 1, "extrapolated"
+            a = (np.log(den_rms) - lr_[j - 1]) / (lr_[j] - lr_[j - 1])
+            n_eq = float(np.exp(ln_[j - 1] + a * (ln_[j] - ln_[j - 1])))
+            t_eq = float(np.exp(lt_[j - 1] + a * (lt_[j] - lt_[j - 1])))
+        den_ms = walk_in_ms + apply_ms
+        tflops = fwd_flop * n_t / (apply_ms * 1e-3) / 1e12
+        print(json.dumps({
+            "study": "denoise", "volumes": "64x64x64 mm, 1-3 ellipsoids, random optics (c5)",
+            "feature_channels": n_aux,
+            "train_volumes": len(train_v), "test_volumes": n_t, "photons_input": args.dn_in,
+            "photons_target": args.dn_target, "photons_reference": args.dn_ref,
+            "data_walk_ms": ms_in + ms_tg, "data_wall_s": gen_s,
+            "train_steps": steps, "train_batch": batch, "train_lr": lr, "train_s": train_s,
+            "train_ms_per_step": 1e3 * train_s / max(steps, 1),
+            "loss_first": float(np.mean(losses[:20])), "loss_last": float(np.mean(losses[-50:])),
+            "ladder_photons": ladder, "ladder_rms": plain_rms, "ladder_walk_ms": plain_ms,
+            "input_rms": plain_rms[0], "denoised_rms": den_rms,
+            "plain_photons_for_denoised_rms": n_eq, "plain_ms_for_denoised_rms": t_eq, "equal_error": how,
+            "denoised_ms": den_ms, "denoised_walk_ms": walk_in_ms, "denoiser_apply_ms": apply_ms,
+            "time_fraction_of_plain": den_ms / t_eq if t_eq else None,
+            "apply_tflops": tflops, "bf16_peak_tflops": pk["bf16_tflops"],
+            "apply_frac_of_peak": tflops / pk["bf16_tflops"] if pk["bf16_tflops"] else None,
+        }), flush=True)
+        d.close()
 
 
 def study_denoise_kernels(args):
@@ -467,6 +473,9 @@ def main():
     ap.add_argument("--dn-batch", type=int, default=4)
     ap.add_argument("--dn-lr", type=float, default=1e-3)
     ap.add_argument("--dn-seed", type=int, default=7)
+    ap.add_argument("--dn-configs", default="",
+                    help="training configurations steps:batch:lr, comma separated (default: "
+                         "--dn-steps:--dn-batch:--dn-lr)")
     ap.add_argument("--dn-aux", type=int, default=0, choices=[0, 2],
                     help="medium-feature input channels (log mua, log reduced mus)")
     args = ap.parse_args()

@@ -205,3 +205,16 @@ def test_encode_decode_inverse_and_log_rms():
     err = od.log_rms(np.array([10.0, 1e-2, 5.0, 7.0]), ref)
     assert err == pytest.approx(np.sqrt(np.mean(np.log10([(10 + 1e-8) / (1 + 1e-8), (1e-2 + 1e-8) / (1e-3 + 1e-8)]) ** 2)),
                                 rel=1e-9)
+
+
+def test_study_log_rms_matches_oracle_definition():
+    """the product's evaluation metric (paper_1711_03244_gb300.denoise.log_rms) against the
+    oracle's restatement on random maps with zeros and a masked tail"""
+    from paper_1711_03244_gb300 import denoise as dn
+    rng = np.random.default_rng(21)
+    ref = 10.0 ** rng.uniform(-9, 0, size=(8, 8, 8))
+    ref[0, 0, :4] = 0.0
+    phi = ref * 10.0 ** rng.normal(0, 0.3, size=ref.shape)
+    phi[1, 1, :5] = 0.0
+    assert dn.log_rms(phi, ref) == pytest.approx(od.log_rms(phi, ref), rel=1e-12)
+    assert dn.log_rms(ref, ref) == 0.0
