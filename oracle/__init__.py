@@ -8,7 +8,8 @@ generators, which hold none of the method's arithmetic).
 
 Parity status of each oracle function (what pins it, see tests/test_oracle_pins.py):
   * RNG (SplitMix64 seeding, xorshift128+ uniforms): SplitMix64 published test vector;
-    uniform moments, range and exact float representability.
+    uniform moments, range and exact float representability; the pair and triple draws
+    against the bit fields of the single draws of the same outputs.
   * orc_hg_cos: mean cosine = g, chi^2 against the HG density, isotropic limit.
   * orc_rotate: unit norm, deflection cosine, azimuth uniformity, vertical special case.
   * orc_fresnel_R: normal-incidence closed form, the independent sine/tangent form of the
@@ -119,6 +120,9 @@ def lib():
         L.orc_uniform_pairs.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_void_p]
         L.orc_uniform_pairs.restype = None
+        L.orc_uniform_triples.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_void_p]
+        L.orc_uniform_triples.restype = None
         L.orc_hg_cos.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_hg_cos.restype = ctypes.c_double
         L.orc_rotate.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
@@ -148,6 +152,13 @@ def uniform_pairs(seed: int, photon: int, n: int) -> np.ndarray:
     out = np.empty(2 * n, dtype=np.float64)
     lib().orc_uniform_pairs(seed, photon, n, out.ctypes.data)
     return out.reshape(n, 2)
+
+
+def uniform_triples(seed: int, photon: int, n: int) -> np.ndarray:
+    """n triple draws (three uniforms from one generator output each), shape [n, 3]."""
+    out = np.empty(3 * n, dtype=np.float64)
+    lib().orc_uniform_triples(seed, photon, n, out.ctypes.data)
+    return out.reshape(n, 3)
 
 
 def hg_cos(g: float, xi: float) -> float:

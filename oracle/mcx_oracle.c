@@ -31,9 +31,10 @@
  * Random numbers.  Each photon has its own xorshift128+ stream (Vigna, "Further
  * scramblings of Marsaglia's xorshift generators", shifts 23/18/5), seeded from the
  * SplitMix64 sequence of the run seed (Steele, Lea & Flood 2014): photon p takes outputs
- * number 2p+1 and 2p+2.  Events that need one uniform (hop, Fresnel, roulette) take the
- * top 23 bits of one output; events that need two (Gaussian launch point, scattering)
- * take the top 23 bits and bits 40..18 of one output.  This is the per-thread
+ * number 2p+1 and 2p+2.  Events that need one uniform (the first hop, Fresnel, roulette)
+ * take the top 23 bits of one output; the Gaussian launch point takes two, the top 23
+ * bits and bits 40..18; a scattering event takes three from one output, bits 63..43,
+ * 42..22 and 21..1 (deflection, azimuth, and the next hop).  This is the per-thread
  * independent seeding of the paper's workflow, made per photon so a run is a pure
  * function of (seed, photon ids).
  * ---------------------------------------------------------------------------------- */
@@ -87,6 +88,16 @@ static void rng_uniform_pair(orc_rng *g, double *u1, double *u2)
     *u2 = (double)(2 * ((r >> 18) & 0x7FFFFFULL) + 1) * (1.0 / 16777216.0);
 }
 
+/* three uniforms from one output, for a scattering event (deflection, azimuth, next
+   hop): bits 63..43, 42..22 and 21..1, each as (2k+1) 2^-22 */
+static void rng_uniform_triple(orc_rng *g, double *u1, double *u2, double *u3)
+{
+    const uint64_t r = rng_next(g);
+    *u1 = (double)(2 * (r >> 43) + 1) * (1.0 / 4194304.0);
+    *u2 = (double)(2 * ((r >> 22) & 0x1FFFFFULL) + 1) * (1.0 / 4194304.0);
+    *u3 = (double)(2 * ((r >> 1) & 0x1FFFFFULL) + 1) * (1.0 / 4194304.0);
+}
+
 void orc_uniforms(uint64_t seed, uint64_t photon, uint64_t n, double *out)
 {
     orc_rng g;
@@ -99,6 +110,13 @@ void orc_uniform_pairs(uint64_t seed, uint64_t photon, uint64_t n, double *out)
     orc_rng g;
     rng_init(&g, seed, photon);
     for (uint64_t i = 0; i < n; ++i) rng_uniform_pair(&g, &out[2 * i], &out[2 * i + 1]);
+}
+
+void orc_uniform_triples(uint64_t seed, uint64_t photon, uint64_t n, double *out)
+{
+    orc_rng g;
+    rng_init(&g, seed, photon);
+    for (uint64_t i = 0; i < n; ++i) rng_uniform_triple(&g, &out[3 * i], &out[3 * i + 1], &out[3 * i + 2]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -370,8 +388,8 @@ static void run_photon(const orc_problem *P, uint64_t id, orc_ctx *C, orc_exit *
         } else {                             /* scattering event */
             C->count[ORC_C_SCATTER]++;
             ++nscat;
-            double xi_hg, xi_phi;
-            rng_uniform_pair(&rng, &xi_hg, &xi_phi);
+            double xi_hg, xi_phi, u_hop;
+            rng_uniform_triple(&rng, &xi_hg, &xi_phi, &u_hop);
             const double ct = orc_hg_cos(g, xi_hg);
             const double ph = 2.0 * ORC_PI * xi_phi;
             double nd[3];
@@ -387,6 +405,10 @@ static void run_photon(const orc_problem *P, uint64_t id, orc_ctx *C, orc_exit *
                     C->tally[ORC_T_RR_KILLED] += w;
                     fate = ORC_FATE_ROULETTE;
                 }
+            }
+            if (fate == ORC_FATE_NONE) {     /* the next hop, drawn with the deflection */
+                s = -log(u_hop);
+                C->count[ORC_C_HOPS]++;
             }
         }
     }

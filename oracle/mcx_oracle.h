@@ -96,6 +96,7 @@ int orc_run(const orc_problem *p, orc_result *r);
 uint64_t orc_splitmix64_output(uint64_t seed, uint64_t k);      /* k-th output, k >= 1 */
 void orc_uniforms(uint64_t seed, uint64_t photon, uint64_t n, double *out);
 void orc_uniform_pairs(uint64_t seed, uint64_t photon, uint64_t n, double *out);  /* 2n values */
+void orc_uniform_triples(uint64_t seed, uint64_t photon, uint64_t n, double *out);  /* 3n values */
 double orc_hg_cos(double g, double xi);
 void orc_rotate(const double u[3], double cos_t, double phi, double out[3]);
 double orc_fresnel_R(double n1, double n2, double cos_i);       /* returns 1 on TIR */

@@ -359,8 +359,9 @@ def mcx_run_noalloc(labels_dev, voxel_mm: float, media, src_kind: int, pos, dire
 
 
 def mcx_debug_uniforms(seed: int, photon: int, n: int) -> np.ndarray:
-    """[n, 2]: per generator output, the single draw and the pair's second value."""
-    out = np.zeros((n, 2), dtype=np.float32)
+    """[n, 5]: per generator output, the single draw, the pair's second value and the
+    three values of a triple draw."""
+    out = np.zeros((n, 5), dtype=np.float32)
     _check(None, load().mcx_debug_uniforms(seed, photon, n, _ptr(out)))
     return out
 

@@ -886,10 +886,10 @@ mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float 
     if (!out_host && n) return fail(nullptr, MCX_E_ARG, "out is NULL");
     if (n == 0) return MCX_OK;
     float *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, 2 * n * sizeof(float));
+    cudaError_t e = cudaMalloc(&d, 5 * n * sizeof(float));
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "allocating");
     e = debug_uniforms(seed, photon, n, d);
-    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, 2 * n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d, 5 * n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e == cudaSuccess ? MCX_OK : cuda_fail(nullptr, e, "debug uniforms");
 }

@@ -110,13 +110,22 @@ struct Rng {
         const uint64_t r = next();
         return from_bits((unsigned)(r >> 41));
     }
-    // Two uniforms from one output (Gaussian launch point, scattering): the top 23 bits
-    // and bits 40..18.
+    // Two uniforms from one output (Gaussian launch point): the top 23 bits and bits
+    // 40..18.
     __device__ __forceinline__ void pair(float &u1, float &u2)
     {
         const uint64_t r = next();
         u1 = from_bits((unsigned)(r >> 41));
         u2 = from_bits((unsigned)(r >> 18) & 0x7fffffu);
+    }
+    // Three uniforms from one output (a scattering event: deflection, azimuth, next hop):
+    // bits 63..43, 42..22 and 21..1, each (2k+1) 2^-22, exactly representable in float.
+    __device__ __forceinline__ void triple(float &u1, float &u2, float &u3)
+    {
+        const uint64_t r = next();
+        u1 = from21((unsigned)(r >> 43));
+        u2 = from21((unsigned)(r >> 22) & 0x1fffffu);
+        u3 = from21((unsigned)(r >> 1) & 0x1fffffu);
     }
     __device__ __forceinline__ uint64_t next()
     {
@@ -132,6 +141,11 @@ struct Rng {
     static __device__ __forceinline__ float from_bits(unsigned k)
     {
         return __uint_as_float(0x3f800000u | k) - 0.99999994039535522461f;
+    }
+    // (1 + k 2^-21) - (1 - 2^-22) = (2k + 1) 2^-22 for a 21-bit k, both steps exact
+    static __device__ __forceinline__ float from21(unsigned k)
+    {
+        return __uint_as_float(0x3f800000u | (k << 2)) - 0.9999997615814208984375f;
     }
 };
 
@@ -607,8 +621,8 @@ walk_kernel(const WalkParams p)
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
                 const MedB<R> B = medB(lab);
-                float xi_hg, xi_phi;
-                rng.pair(xi_hg, xi_phi);
+                float xi_hg, xi_phi, u_hop;
+                rng.triple(xi_hg, xi_phi, u_hop);
                 R ct, st;
                 hg_sample(B, R(xi_hg), ct, st);
                 R sn, cs;
@@ -628,7 +642,10 @@ walk_kernel(const WalkParams p)
                         fate = MCX_FATE_ROULETTE;
                     }
                 }
-                if (fate == MCX_FATE_NONE) new_hop();     // a4: the next hop
+                if (fate == MCX_FATE_NONE) {              // a4: the next hop, drawn with the
+                    const R h = M<R>::hop(R(u_hop));      // deflection
+                    s = h > M<R>::tiny_hop() ? h : M<R>::tiny_hop();
+                }
             }
         }
         if (fate == MCX_FATE_NONE) continue;
@@ -716,7 +733,13 @@ __global__ void uniforms_kernel(uint64_t seed, uint64_t photon, uint64_t n, floa
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     Rng r;
     r.seed(seed, photon);
-    for (uint64_t i = 0; i < n; ++i) r.pair(out[2 * i], out[2 * i + 1]);
+    // per output: the single draw, the pair's second value (from a copy of the state),
+    // then the triple from the same output
+    for (uint64_t i = 0; i < n; ++i) {
+        Rng c = r;
+        c.pair(out[5 * i], out[5 * i + 1]);
+        r.triple(out[5 * i + 2], out[5 * i + 3], out[5 * i + 4]);
+    }
 }
 
 __global__ void primitive_kernel(int kind, uint64_t n, const float *in, float *out)

@@ -67,6 +67,33 @@ def test_uniform_pairs_split_one_output(orc):
     assert chi2 < 31 + 6 * math.sqrt(2 * 31)
 
 
+def test_uniform_triples_split_one_output(orc):
+    """A triple draw (scattering: deflection, azimuth, next hop) consumes one generator
+    output: its fields are bits 63..43, 42..22 and 21..1 of that output, which the single
+    draw (bits 63..41) and the pair's second value (bits 40..18) of the same output fix
+    except for bits 17..1; each value is (2k+1) 2^-22, uniform, and uncorrelated with the
+    others."""
+    n = 20_000
+    single = orc.uniforms(7, 11, n)
+    pairs = orc.uniform_pairs(7, 11, n)
+    tri = orc.uniform_triples(7, 11, n)
+    k_hi = np.round((single * 2 ** 24 - 1) / 2).astype(np.int64)        # bits 63..41
+    k_lo = np.round((pairs[:, 1] * 2 ** 24 - 1) / 2).astype(np.int64)   # bits 40..18
+    t = np.round((tri * 2 ** 22 - 1) / 2).astype(np.int64)
+    assert np.allclose(tri * 2 ** 22, 2 * t + 1, rtol=0, atol=0)
+    assert np.array_equal(t[:, 0], k_hi >> 2)                            # bits 63..43
+    assert np.array_equal(t[:, 1], ((k_hi & 3) << 19) | (k_lo >> 4))   # bits 42..22
+    assert np.array_equal(t[:, 2] >> 17, k_lo & 15)                      # bits 21..18
+    for c in range(3):
+        u = tri[:, c]
+        assert 0 < u.min() and u.max() < 1
+        assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / n)
+        hist, _ = np.histogram(u, bins=32, range=(0, 1))
+        assert ((hist - n / 32) ** 2 / (n / 32)).sum() < 31 + 6 * math.sqrt(2 * 31)
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        assert abs(np.corrcoef(tri[:, a], tri[:, b])[0, 1]) < 5 / math.sqrt(n)
+
+
 def test_uniform_streams_independent_per_photon(orc):
     a = orc.uniforms(7, 0, 2000)
     b = orc.uniforms(7, 1, 2000)
