@@ -412,6 +412,12 @@ mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float 
 mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
                                float *out_host);
 
+/* The bounded mbarrier wait the denoiser's pipelines use, on a barrier that nothing
+   arrives on (arrive = 0: the wait must give up after 2^limit_log2 polls, limit_log2 <= 22)
+   or that one arrival completes first (arrive = 1).  *timed_out = 1 when it gave up.  No
+   device state is left behind either way. */
+mcx_status mcx_debug_wait_timeout(int32_t arrive, int32_t limit_log2, int32_t *timed_out);
+
 /* One 3x3x3 convolution of the denoiser on host arrays, run by the denoiser's own
    tensor-core kernels (tcgen05 for kind 0, warp-level mma for kind 1); values are rounded
    to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16 up to 254:

@@ -153,6 +153,7 @@ SIGNATURES = {
     "mcx_debug_uniforms": (_i32, [_u64, _u64, _u64, _P]),
     "mcx_debug_primitive": (_i32, [_i32, _u64, _P, _P]),
     "mcx_debug_conv3d": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32, _i32, _P, _P, _P, _P, _P]),
+    "mcx_debug_wait_timeout": (_i32, [_i32, _i32, ctypes.POINTER(_i32)]),
 }
 
 _lib = None
@@ -395,6 +396,13 @@ def mcx_debug_conv3d(kind: int, x: np.ndarray, w=None, bias=None, dy=None, cout=
         _check(None, load().mcx_debug_conv3d(1, n, nz, ny, nx, cin, cout, _ptr(xa), None, None,
                                              _ptr(da), _ptr(out)))
     return out
+
+
+def mcx_debug_wait_timeout(arrive: bool, limit_log2: int = 16) -> bool:
+    """True when the bounded mbarrier wait gave up (see include/mcx.h)."""
+    out = ctypes.c_int32()
+    _check(None, load().mcx_debug_wait_timeout(int(bool(arrive)), limit_log2, ctypes.byref(out)))
+    return bool(out.value)
 
 
 def decode_detected(rec: np.ndarray) -> dict:

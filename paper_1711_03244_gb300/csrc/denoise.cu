@@ -161,9 +161,9 @@ __host__ __device__ constexpr int tc_stages(int cin, int cout, int w)
     return 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it) {       // about a second of polling at most
+    for (int it = 0; it < limit; ++it) {            // 1 << 22: about a second of polling
         uint32_t ok;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -915,6 +915,18 @@ __global__ void gather_kernel(const float *set, GatherList L, int n, int D, int 
     }
 }
 
+// the bounded wait on an mbarrier that nothing arrives on (arrive = 0) or that one arrival
+// completes first (arrive = 1): out[0] = 1 when the wait gave up
+__global__ void wait_probe_kernel(int arrive, int limit, unsigned *out)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (arrive) mbar_arrive(b);
+    out[0] = mbar_wait(b, 0u, limit) ? 0u : 1u;
+}
+
 unsigned grid1(long long n)
 {
     return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32));
@@ -1447,6 +1459,19 @@ mcx_status mcx_denoiser_features(const uint8_t *labels_dev, uint64_t nvox, uint3
         DNC(nullptr, cudaGetLastError(), "features");
     }
     DNC(nullptr, cudaStreamSynchronize(st), "waiting for the features");
+    return MCX_OK;
+}
+
+mcx_status mcx_debug_wait_timeout(int32_t arrive, int32_t limit_log2, int32_t *timed_out)
+{
+    if (!timed_out || limit_log2 < 0 || limit_log2 > 22) return dn_fail(nullptr, MCX_E_ARG, "bad arguments");
+    DBuf o;
+    DNC(nullptr, o.alloc(4), "allocating");
+    wait_probe_kernel<<<1, 1>>>(arrive ? 1 : 0, 1 << limit_log2, o.as<unsigned>());
+    DNC(nullptr, cudaGetLastError(), "launching the wait probe");
+    unsigned h = 0;
+    DNC(nullptr, cudaMemcpy(&h, o.p, 4, cudaMemcpyDeviceToHost), "reading the wait probe");
+    *timed_out = (int32_t)h;
     return MCX_OK;
 }
 

@@ -311,3 +311,15 @@ def test_gather_mirrors_and_transposes(g, torch_cuda):
         if flags[s] & 4:
             v = v.transpose(0, 2, 1)
         assert np.array_equal(got[s], v), s
+
+
+def test_bounded_wait_gives_up_and_reports(g):
+    """The pipelines' mbarrier wait on a barrier nothing arrives on gives up after its
+    poll limit (and the context stays usable); with the arrival first it succeeds."""
+    import time
+    t0 = time.time()
+    assert g.mcx_debug_wait_timeout(False, 16) is True
+    assert time.time() - t0 < 30
+    assert g.mcx_debug_wait_timeout(True, 16) is False
+    # the device still runs work afterwards
+    assert g.mcx_debug_wait_timeout(True, 4) is False
