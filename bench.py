@@ -462,14 +462,14 @@ def main():
                          "denoiser and compare denoised and plain runs at equal error; "
                          "denoise-kernels: the denoiser's forward pass and training step "
                          "alone (one JSON line each)")
-    ap.add_argument("--dn-train", type=int, default=512, help="training volumes")
-    ap.add_argument("--dn-test", type=int, default=16, help="held-out volumes")
+    ap.add_argument("--dn-train", type=int, default=4096, help="training volumes")
+    ap.add_argument("--dn-test", type=int, default=64, help="held-out volumes")
     ap.add_argument("--dn-in", type=int, default=100_000, help="photons of an input map")
     ap.add_argument("--dn-target", type=int, default=10_000_000, help="photons of a target map")
     ap.add_argument("--dn-ref", type=int, default=1_000_000_000, help="photons of a reference map")
     ap.add_argument("--dn-ladder-max", type=int, default=100_000_000,
                     help="largest plain run of the equal-error ladder")
-    ap.add_argument("--dn-steps", type=int, default=3000)
+    ap.add_argument("--dn-steps", type=int, default=64000)
     ap.add_argument("--dn-batch", type=int, default=4)
     ap.add_argument("--dn-lr", type=float, default=1e-3)
     ap.add_argument("--dn-seed", type=int, default=7)
