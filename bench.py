@@ -449,8 +449,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--photons", type=int, default=100_000_000)
-    ap.add_argument("--ref-photons", type=int, default=20_000)
-    ap.add_argument("--cpu-photons", type=int, default=50_000)
+    ap.add_argument("--ref-photons", type=int, default=200_000)
+    ap.add_argument("--cpu-photons", type=int, default=1_500_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-model", action="store_true",
