@@ -246,7 +246,11 @@ typedef struct mcx_batch_cfg {
     int32_t use_graph;             /* 1: record the run (zeroing, walk, reductions) as a CUDA
                                       graph on first use and replay it while the batch and the
                                       settings stay the same */
-    int32_t reserved0;
+    int32_t order;                 /* photon queue order: 0 = the simulations as added, 1 =
+                                      (default) the longest expected photon histories first, a
+                                      scheduling heuristic from the optical properties that
+                                      shortens the launch's tail; results do not depend on it
+                                      (each simulation keeps its own photon streams) */
     void *cuda_stream;             /* cudaStream_t (NULL = legacy default; with use_graph the
                                       library then uses a stream of its own) */
 } mcx_batch_cfg;

@@ -88,7 +88,7 @@ class McxBatchCfg(ctypes.Structure):
         ("grid_size", ctypes.c_int32),
         ("max_events_per_photon", ctypes.c_uint64),
         ("use_graph", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("order", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p),
     ]
 

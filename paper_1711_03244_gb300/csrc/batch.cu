@@ -92,8 +92,32 @@ struct SimHost {
     int kind;
     double pos[3], dir[3], waist;
     uint64_t n_photons, seed;
+    std::vector<double> frac;     // volume fraction of each label
     Buf labels;
 };
+
+// Expected work of the longest photon histories of a simulation, for ordering the queue
+// (a scheduling heuristic, not part of the method).  Per label: photons are lost at the
+// rate mua + pi^2 / (L^2 mus') per unit path (absorption, and escape by diffusion from a
+// cube of the grid's mean side L: the slowest mode's loss rate, mus' = mus (1 - g)), so the
+// longest of N photons travels about ln(N) / rate, or up to the time window; times the
+// events per unit path (scatterings mus and voxel crossings 1 / h), weighted by the label's
+// volume fraction.  Starting these photons first keeps them out of the launch's tail.
+double photon_cost(const SimHost *s, uint32_t n_gates, float dt_ns)
+{
+    const double L = s->h * (s->nx + s->ny + s->nz) / 3.0;
+    const double ln_n = std::log(std::max<double>((double)s->n_photons, 2.0));
+    double c = 0.0;
+    for (uint32_t l = 1; l < s->n_media && l < s->frac.size(); ++l) {
+        if (s->frac[l] <= 0.0) continue;
+        const double mua = s->props[4 * l], mus = s->props[4 * l + 1], g = s->props[4 * l + 2];
+        const double n = s->props[4 * l + 3], musp = std::max(mus * (1.0 - g), 1e-6);
+        const double rate = mua + 9.8696044 / (L * L * musp);
+        const double path = std::min(ln_n / std::max(rate, 1e-9), 299.792458 / n * n_gates * dt_ns);
+        c += s->frac[l] * path * (mus + 1.0 / s->h);
+    }
+    return c;
+}
 
 }  // namespace
 
@@ -150,6 +174,7 @@ void mcx_batch_cfg_default(mcx_batch_cfg *c)
     c->rr_threshold = 1e-4f;
     c->rr_m = 10.f;
     c->accum_mode = 2;
+    c->order = 1;
 }
 
 mcx_status mcx_batch_create(mcx_batch **out)
@@ -217,6 +242,9 @@ mcx_status mcx_batch_add(mcx_batch *b, uint32_t nx, uint32_t ny, uint32_t nz, fl
         delete s;
         return bfail(b, MCX_E_STATE, "the volume has a label without a media row");
     }
+    s->frac.assign(n_media, 0.0);
+    for (const uint8_t l : host) s->frac[l] += 1.0;
+    for (double &f : s->frac) f /= (double)nv;
     if (s->labels.ensure(nv) != cudaSuccess ||
         cudaMemcpy(s->labels.p, host.data(), nv, cudaMemcpyHostToDevice) != cudaSuccess) {
         delete s;
@@ -253,9 +281,19 @@ static mcx_status layout(mcx_batch *b, const mcx_batch_cfg *cfg, double fraction
     std::vector<unsigned char> A(16 * (size_t)rows), B(16 * (size_t)rows), N(4 * (size_t)rows),
         T(4 * (size_t)rows);
     std::vector<unsigned char> tmp;
+    // queue order: as added, or the longest expected photon histories first (their
+    // photons then start early instead of forming the tail of the launch)
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    if (cfg->order == 1) {
+        std::vector<double> cost(n);
+        for (size_t i = 0; i < n; ++i) cost[i] = photon_cost(b->sims[i], cfg->n_gates, cfg->dt_ns);
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
+    }
+    std::vector<size_t> slot(n);
+    for (size_t k = 0; k < n; ++k) slot[order[k]] = k;
     std::vector<BatchSim> d(n);
     int row = 0;
-    uint64_t first = 0;
     for (size_t i = 0; i < n; ++i) {
         const SimHost *s = b->sims[i];
         tmp.assign(walk_table_bytes(Precision::F32, (int)s->n_media), 0);
@@ -266,16 +304,14 @@ static mcx_status layout(mcx_batch *b, const mcx_batch_cfg *cfg, double fraction
         std::memcpy(&B[16 * (size_t)row], tmp.data() + (size_t)ob, 16 * s->n_media);
         std::memcpy(&N[4 * (size_t)row], tmp.data() + (size_t)on, 4 * s->n_media);
         std::memcpy(&T[4 * (size_t)row], tmp.data() + (size_t)ot, 4 * s->n_media);
-        BatchSim &D = d[i];
+        BatchSim &D = d[slot[i]];
         D.labels = s->labels.as<uint8_t>();
         D.fluence = elt == sizeof(float) ? b->fluence.as<float>() + b->flu_off[i] : nullptr;
         D.fluence64 = elt == sizeof(double) ? b->fluence.as<double>() + b->flu_off[i] : nullptr;
         D.tally = b->tallies.as<double>() + i * MCX_NTALLY;
-        D.first = first;
         D.n_photons = fraction >= 1.0 ? s->n_photons
                                       : (uint64_t)std::max(1.0, std::round((double)s->n_photons * fraction));
         if (s->n_photons == 0) D.n_photons = 0;
-        first += D.n_photons;
         D.seed = s->seed;
         D.nx = (int)s->nx; D.ny = (int)s->ny; D.nz = (int)s->nz;
         D.nvox = s->nx * s->ny * s->nz;
@@ -291,6 +327,11 @@ static mcx_status layout(mcx_batch *b, const mcx_batch_cfg *cfg, double fraction
         }
         D.waist = (float)(s->waist / s->h);
         row += (int)s->n_media;
+    }
+    uint64_t first = 0;                       // flattened photon ids, in queue order
+    for (size_t k = 0; k < n; ++k) {
+        d[k].first = first;
+        first += d[k].n_photons;
     }
     BCUDA(b, b->tab_a.ensure(A.size()), "allocating tables");
     BCUDA(b, b->tab_b.ensure(B.size()), "allocating tables");
@@ -366,6 +407,7 @@ static mcx_status check_cfg(mcx_batch *b, const mcx_batch_cfg *cfg)
     if (cfg->claim_chunk && (cfg->claim_chunk < 32 || cfg->claim_chunk > 4096))
         return bfail(b, MCX_E_ARG, "claim_chunk 32..4096");
     if (cfg->grid_size < 0) return bfail(b, MCX_E_ARG, "grid_size < 0");
+    if (cfg->order != 0 && cfg->order != 1) return bfail(b, MCX_E_ARG, "order is 0 or 1");
     return MCX_OK;
 }
 
@@ -396,7 +438,7 @@ mcx_status mcx_batch_run(mcx_batch *b, const mcx_batch_cfg *cfg)
                                      cfg->n_gates, cfg->dt_ns, cfg->reflect, cfg->rr_threshold,
                                      cfg->rr_m, cfg->max_events_per_photon, (void *)stream);
     if (b->dirty || !b->ran || key != b->graph_key || cfg->accum_mode != b->cfg.accum_mode ||
-        cfg->n_gates != b->cfg.n_gates)
+        cfg->n_gates != b->cfg.n_gates || cfg->order != b->cfg.order)
         drop_graph(b);
     LaunchShape shape;
     st = prepare(b, cfg, &shape);

@@ -133,3 +133,23 @@ def test_c4_batch_256_simulations(g):
         print(f"c4: {len(sims)} simulations, {total:.3e} photons in {ms:.0f} ms "
               f"= {total / ms:.0f} photons/ms; worst energy balance {worst:.1e}")
         assert worst < 1e-5
+
+
+def test_queue_order_does_not_change_results(g):
+    """Longest-expected-histories-first queue order (the default) against the order of
+    addition: every simulation keeps its photon streams, so tallies and maps agree to the
+    FP64 summation order."""
+    sims = [f32(w) for w in workloads.c4(n_sims=8)]
+    sims = [w.with_(n_photons=min(w.n_photons, 50_000)) for w in sims]
+    res = {}
+    with g.Batch() as b:
+        for wl in sims:
+            b.add_workload(wl)
+        for order in (0, 1):
+            b.run(n_gates=5, dt_ns=1.0, order=order)
+            res[order] = ([b.tally(i) for i in range(len(sims))],
+                          [b.fluence(i).astype(np.float64) for i in range(len(sims))])
+    for i in range(len(sims)):
+        for k in res[0][0][i]:
+            assert res[1][0][i][k] == pytest.approx(res[0][0][i][k], rel=1e-12, abs=1e-12)
+        assert np.allclose(res[1][1][i], res[0][1][i], rtol=1e-6, atol=0)
