@@ -634,7 +634,7 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write)",
                        "accumulation": "FP64 L2 atomics per (gate, voxel) run (accum_mode 2)",
                        "launch": info, "parallelism": f"photon-id ranges x{world}"},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,       # per mcx_run: 3 zeroing, the walk, the tally reduction
             "wall_s": wall,
             "clocks": clk.summary(),
             "roofline": roof,
