@@ -187,7 +187,7 @@ def run_reference(args, wl, world, rank):
 def study_paper(args):
     """The paper's benchmarks (60 mm cube, pencil beam, 1e8 photons; B2/B2a with the
     r = 15 mm sphere; B1 terminates at the boundary), each step timed like the main bench.
-    Rows: accumulation plain FP32 / FP64 / compensated tiles (this build's counterpart of
+    Rows: accumulation plain FP32 / FP64 / compensated tiles (the library's counterpart of
     the paper's non-atomic B2 vs atomic B2a comparison: B2's racy adds are not built), and
     photon distribution dynamic vs the static per-thread split (the paper's Fig. 3a)."""
     import torch

@@ -207,7 +207,7 @@ def paper_b(variant: str = "B1", n_photons: int = 100_000_000, seed: int = 12345
     pencil beam at (30,30,0) +z.  B2/B2a add a central r=15 mm sphere (mua 0.002, mus 5.0,
     g 0.9, n 1.0).  B1 terminates photons at the cube boundary (no reflection); B2/B2a
     apply Fresnel/Snell at the sphere and cube boundaries.  (B2 and B2a differ only in
-    non-atomic vs atomic accumulation; this build always accumulates race-free.)
+    non-atomic vs atomic accumulation; the library always accumulates race-free.)
     The paper states no time window; one 0-5 ns gate is used here (reading)."""
     labels = np.ones((60, 60, 60), dtype=np.uint8)
     media = [AIR, (0.005, 1.0, 0.01, 1.37)]
