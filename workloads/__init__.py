@@ -179,8 +179,10 @@ def c4(n_sims: int = 256, seed: int = 1711032440) -> List[Workload]:
 def c5(n_volumes: int, seed: int, n_photons: int = 100_000) -> List[Workload]:
     """Seeded 64 mm cubes for the learned denoiser, drawn like c4 with the side fixed at
     64: 1-3 random axis-aligned ellipsoids, random optical properties, pencil source at a
-    random point of the z=0 face, one 0-5 ns gate.  Disjoint seeds give disjoint training
-    and held-out sets; the simulation seed of volume k is seed + 1 + k."""
+    random point of the z=0 face, one 0-5 ns gate.  Different generator seeds give
+    different volumes (training and held-out sets); the simulation seed of volume k is
+    seed + 1 + k, so consecutive generator seeds share photon streams between different
+    volumes, which differ in geometry and optics (the trajectories do not coincide)."""
     rng = np.random.default_rng(seed)
     side = 64
     out = []
