@@ -266,11 +266,20 @@ def study_batched(args):
             e1.record(stream)
             e1.synchronize()
             seq_ms += e0.elapsed_time(e1)
+    # the batch walk against the same issue roofline as the main bench line
+    pk = peaks()
+    ops = algorithmic_ops(stats, None)
+    peak = SM_COUNT * LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved = ops / (min(ms) * 1e-3) / 1e12
     print(json.dumps({"study": "batched", "simulations": len(sims), "photons": total,
                       "autotuned": best, "batch_ms_best": min(ms),
                       "batch_photons_per_ms": total / min(ms),
                       "sequential_ms": seq_ms, "sequential_photons_per_ms": total / seq_ms,
-                      "speedup": seq_ms / min(ms), "photons_simulated": stats["photons"]}),
+                      "speedup": seq_ms / min(ms), "photons_simulated": stats["photons"],
+                      "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                                   "unit": "Tthread-op/s", "frac": achieved / peak,
+                                   "ops_per_photon": ops / max(stats["photons"], 1),
+                                   "note": "whole graph replay (zeroing, walk, reductions)"}}),
           flush=True)
 
 
