@@ -6,11 +6,12 @@
  * Photon loop (paper: "a photon simulation loop is carried out within each computing
  * thread", workflow paragraph beside Fig. 1; physics per the benchmark description beside
  * Fig. 2 and the MCML formulation):
- *   launch -> repeat { draw a hop if the previous one is used up; move to the nearest of
- *   (voxel face, scattering point, end of the time window); deposit the absorbed weight
- *   w(1 - exp(-mua l)) in the (gate, voxel) of the segment start; then handle the event:
- *   time-out, face (pass / Fresnel reflect / refract / escape + detector), or scatter
- *   (Henyey-Greenstein + rotation, then Russian roulette) }.
+ *   launch -> repeat { draw a hop if none is pending (the first one, or one that rounding
+ *   used up at a face); move to the nearest of (voxel face, scattering point, end of the
+ *   time window); deposit the absorbed weight w(1 - exp(-mua l)) in the (gate, voxel) of
+ *   the segment start; then handle the event: time-out, face (pass / Fresnel reflect /
+ *   refract / escape + detector), or scatter (Henyey-Greenstein + rotation with the next
+ *   hop drawn alongside, then Russian roulette) }.
  *
  * Readings where the paper is silent are listed in the project's design notes; the main
  * ones are repeated at the place they apply.
