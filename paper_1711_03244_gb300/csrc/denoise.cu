@@ -404,6 +404,223 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     }
 }
 
+// Layers whose weights do not fit in shared memory (more than 64 KiB: cin x cout of 96 x 32,
+// 64 x 64, ...) run weights-stationary: a work unit is TU consecutive tiles with one
+// accumulator each (two units' worth of tensor memory, so one unit's read-out overlaps the
+// next unit's MMAs), and the unit goes through the planes dz = -1, 0, +1 in turn: the
+// plane's 9 taps of weights are loaded once (one buffer, refilled when the previous
+// plane's MMAs have completed), then each tile's window of that plane streams through
+// the ring.  Weights then cross L2 once per unit and plane instead of once per tile and
+// plane.  Tiles, windows, operand layouts and the bounded waits are those of
+// conv3d_fwd_tc.
+constexpr int kWsHeader = 512;
+
+__host__ __device__ constexpr int ws_tiles_per_unit(int cout)
+{
+    return cout <= 32 ? 8 : (cout <= 64 ? 4 : 2);          // 2 x TU x columns = 512
+}
+__host__ __device__ constexpr int ws_smem_bytes(int cin, int cout, int w, int ns)
+{
+    return 1024 + kWsHeader + 9 * cout * cin * 2 + ns * (cin / 8) * tc_lbo_a(w);
+}
+__host__ __device__ constexpr int ws_stages(int cin, int cout, int w)
+{
+    for (int ns = 6; ns >= 2; --ns)
+        if (ws_smem_bytes(cin, cout, w, ns) <= kTcSmemMax) return ns;
+    return 0;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kTcThreads)
+conv3d_fwd_ws(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+              const float *__restrict__ bias, Vol v, int relu, bf16 *__restrict__ Y, unsigned *err, int ns)
+{
+    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns per accumulator
+    constexpr int TU = ws_tiles_per_unit(COUT);
+    constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
+    // header: full[ns] at 0, empty[ns] at 64, acc full[2 TU] at 128, acc empty[2 TU] at 256,
+    // weights full at 384, weights empty at 392, TMEM address at 448
+    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 256;
+    const uint32_t wfull = base + 384, wempty = base + 392;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 448 - smem_u32(smem_raw)));
+    const int wtap = COUT * CIN * 2, lbo_b = COUT * 16;
+    const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
+    const int a_bytes = (CIN / 8) * lbo_a;
+    const uint32_t wbuf = base + kWsHeader;                // one plane's 9 taps
+    const uint32_t ring = wbuf + 9 * wtap;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
+    const int n_tiles = v.n * v.d * tiles_plane;
+    const int n_units = (n_tiles + TU - 1) / TU;
+    const int my_units = n_units > (int)blockIdx.x ? (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    struct Tl { int b, z, q0; };
+    auto tile_at = [&](int tile) {
+        const int plane = tile / tiles_plane;
+        return Tl{plane / v.d, plane % v.d, (tile % tiles_plane) * kTcRows};
+    };
+    auto unit_tiles = [&](int uj, int &t0, int &nt) {
+        const int u = (int)blockIdx.x + uj * (int)gridDim.x;
+        t0 = u * TU;
+        nt = min(TU, n_tiles - t0);
+    };
+    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(tslot)), "r"(2 * TU * NCOL) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < ns; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, 1);
+        }
+        for (int a = 0; a < 2 * TU; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4 * 32);
+        }
+        mbar_init(wfull, 1);
+        mbar_init(wempty, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (tid == 0) {
+        // ------------------------------------------------------------ producer (TMA)
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmw)) : "memory");
+        const uint32_t tx = (CIN / 8) * (L * PW * 16);
+        int b = 0, use = 0, wpass = 0;
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            int t0, nt;
+            unit_tiles(uj, t0, nt);
+            for (int g = 0; g < 3 && ok; ++g) {               // plane z + g - 1
+                if (wpass > 0) ok &= mbar_wait(wempty, (uint32_t)((wpass - 1) & 1));
+                if (!ok) break;
+                mbar_expect_tx(wfull, 9 * wtap);
+                for (int tt = 0; tt < 9; ++tt)
+                    for (int c = 0; c < CIN / 8; ++c)
+                        tma_load_2d(wbuf + tt * wtap + c * lbo_b, &tmw, 8 * c, (9 * g + tt) * COUT, wfull);
+                ++wpass;
+                for (int t = 0; t < nt && ok; ++t) {
+                    if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
+                    if (!ok) break;
+                    const Tl T = tile_at(t0 + t);
+                    const uint32_t st = ring + b * a_bytes, fb = full0 + 8 * b;
+                    mbar_expect_tx(fb, tx);
+                    for (int c = 0; c < CIN / 8; ++c)
+                        tma_load_5d(st + c * lbo_a, &tmx, 8 * c, -1, first_line(T.q0), T.z + g - 1, T.b, fb);
+                    if (++b == ns) { b = 0; ++use; }
+                }
+            }
+        }
+        for (int bb = 0; bb < ns; ++bb) {                     // every load has landed
+            const int issued = use + (bb < b ? 1 : 0);
+            if (issued > 0) ok &= mbar_wait(full0 + 8 * bb, (uint32_t)((issued - 1) & 1));
+        }
+        if (wpass > 0) ok &= mbar_wait(wfull, (uint32_t)((wpass - 1) & 1));
+    } else if (tid == 32) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint64_t adesc0 = umma_desc(ring, lbo_a, 128);
+        const uint64_t bdesc0 = umma_desc(wbuf, lbo_b, 128);
+        int toff[9];
+#pragma unroll
+        for (int tt = 0; tt < 9; ++tt) toff[tt] = (tt / 3 - 1) * PW + (tt % 3 - 1);
+        int b = 0, use = 0, wpass = 0;
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            int t0, nt;
+            unit_tiles(uj, t0, nt);
+            const int set = uj & 1;
+            for (int g = 0; g < 3 && ok; ++g) {
+                ok &= mbar_wait(wfull, (uint32_t)(wpass & 1));
+                if (!ok) break;
+                for (int t = 0; t < nt && ok; ++t) {
+                    const int slot = set * TU + t;
+                    if (g == 0 && uj >= 2)                      // the slot's previous tile is read out
+                        ok &= mbar_wait(acce0 + 8 * slot, (uint32_t)(((uj >> 1) - 1) & 1));
+                    ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const Tl T = tile_at(t0 + t);
+                    const int off = T.q0 - first_line(T.q0) * PW;
+                    const uint64_t abase = adesc0 + (uint64_t)((b * a_bytes + off * 16) >> 4);
+                    const uint32_t d = tmem + slot * NCOL;
+#pragma unroll
+                    for (int tt = 0; tt < 9; ++tt)
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                            const uint64_t bd = bdesc0 + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
+                            const uint32_t accum = (g == 0 && tt == 0 && kk == 0) ? 0u : 1u;
+                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                         ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
+                        }
+                    tc_commit(empty0 + 8 * b);
+                    if (g == 2) tc_commit(accf0 + 8 * slot);    // tile t of the unit is complete
+                    if (++b == ns) { b = 0; ++use; }
+                }
+                tc_commit(wempty);                              // this plane's weights are free
+                ++wpass;
+            }
+        }
+    } else if (warp >= 2) {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
+        for (int uj = 0; uj < my_units && ok; ++uj) {
+            int t0, nt;
+            unit_tiles(uj, t0, nt);
+            for (int t = 0; t < nt && ok; ++t) {
+                const int slot = (uj & 1) * TU + t;
+                ok &= mbar_wait(accf0 + 8 * slot, (uint32_t)((uj >> 1) & 1));
+                ok = __all_sync(0xffffffffu, ok);               // the collective reads below
+                if (!ok) break;
+                tc_fence_after();
+                float a[COUT];
+                const uint32_t taddr = tmem + slot * NCOL + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+                for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16(taddr + c0, a + c0);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(acce0 + 8 * slot);
+                const Tl T = tile_at(t0 + t);
+                const int q = T.q0 + r, y = q / PW, x = q - y * PW - 1;
+                if (y < v.h && x >= 0 && x < v.w) {
+                    bf16 *yr = Y + ((((long long)T.b * v.d + T.z) * v.h + y) * v.w + x) * COUT;
+#pragma unroll
+                    for (int c = 0; c < COUT; c += 8) {
+                        float o[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            o[e] = a[c + e] + (bias ? __ldg(bias + c + e) : 0.f);
+                            if (relu) o[e] = fmaxf(o[e], 0.f);
+                        }
+                        uint4 pk;
+                        pk.x = pack_bf16(o[0], o[1]);
+                        pk.y = pack_bf16(o[2], o[3]);
+                        pk.z = pack_bf16(o[4], o[5]);
+                        pk.w = pack_bf16(o[6], o[7]);
+                        *reinterpret_cast<uint4 *>(yr + c) = pk;
+                    }
+                }
+            }
+        }
+    }
+    if (!__syncthreads_and(ok) && tid == 0) atomicOr(err, 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * TU * NCOL) : "memory");
+    }
+}
+
 // Weight gradient: dW[tap][co][ci] = sum_p dY[p][co] X[p + off(tap)][ci], over the same
 // tiles and windows as the forward kernel (positions q along padded lines; the dY tile's
 // pad rows come in as zeros from the tensor map, so the windows' pad and neighbour rows
@@ -972,6 +1189,24 @@ cudaError_t launch_tc_t(const bf16 *X, const bf16 *W, const float *bias, Vol v, 
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
+    if constexpr (!tc_wall(CIN, COUT)) {
+        // weights too large to keep: the weights-stationary kernel, one CTA per SM (its
+        // two units of accumulators take the SM's 512 tensor-memory columns)
+        const int wns = ws_stages(CIN, COUT, v.w);
+        if (wns < 2) return cudaErrorInvalidValue;
+        const int wsmem = ws_smem_bytes(CIN, COUT, v.w, wns);
+        cudaError_t we = cudaFuncSetAttribute(conv3d_fwd_ws<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem);
+        if (we != cudaSuccess) return we;
+        int wdev = 0, wsms = 0;
+        if ((we = cudaGetDevice(&wdev)) != cudaSuccess) return we;
+        if ((we = cudaDeviceGetAttribute(&wsms, cudaDevAttrMultiProcessorCount, wdev)) != cudaSuccess) return we;
+        const long long wtiles = (long long)v.n * v.d * ((v.h * (v.w + 2) + kTcRows - 1) / kTcRows);
+        if (wtiles * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
+        const long long wunits = (wtiles + ws_tiles_per_unit(COUT) - 1) / ws_tiles_per_unit(COUT);
+        const unsigned wblocks = (unsigned)std::max<long long>(1, std::min<long long>(wunits, wsms));
+        conv3d_fwd_ws<CIN, COUT><<<wblocks, kTcThreads, wsmem, st>>>(mx, mw, bias, v, relu, Y, err, wns);
+        return cudaGetLastError();
+    }
     const int ns = tc_stages(cin, COUT, v.w);
     if (ns < 2) return cudaErrorInvalidValue;                   // the volume is too wide
     const int smem = tc_smem_bytes(cin, COUT, v.w, ns);
