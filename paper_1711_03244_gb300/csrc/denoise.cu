@@ -865,29 +865,44 @@ __device__ __forceinline__ void children_of(int pc, const Vol &vf, int *ch)
 #define GRID_LOOP(i, n) \
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
 
-// ReLU backward: zero the gradient where the stored output is not positive
-__global__ void relu_mask(bf16 *dY, const bf16 *Y, int n8)
+// ReLU backward fused with the bias gradient: zero dY where the stored output is not
+// positive and add what survives into db[channel].  Chunk i holds channels
+// 8 (i mod C/8) .. +7 of position i / (C/8); the grid stride is a multiple of 256 chunks,
+// so each thread keeps one 8-channel group and sums it in registers, then lanes of the
+// same group, then the block's warps, with one atomic per channel per block.
+template <int C>
+__global__ void __launch_bounds__(256) relu_bias_grad(bf16 *dY, const bf16 *Y, int n8, float *db)
 {
+    static_assert(C % 8 == 0 && 32 % (C / 8) == 0, "8-channel groups must tile a warp");
+    constexpr int G = C / 8;
+    __shared__ float red[8][C];
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     GRID_LOOP(i, n8) {
         float y[8], g[8];
-        Bf8{ld16(Y + 8 * i)}.to(y);
-        Bf8{ld16(dY + 8 * i)}.to(g);
+        Bf8{ld16(Y + 8 * (size_t)i)}.to(y);
+        Bf8{ld16(dY + 8 * (size_t)i)}.to(g);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 8; ++k) {
             if (y[k] <= 0.f) g[k] = 0.f;
-        st16(dY + 8 * i, Bf8::from(g).u);
+            acc[k] += g[k];
+        }
+        st16(dY + 8 * (size_t)i, Bf8::from(g).u);
     }
-}
-
-__global__ void bias_grad(const bf16 *dY, int npos, int c, float *db)
-{
-    // one block column per channel, a slice of positions per thread
-    const int ch = blockIdx.y;
-    float s = 0.f;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += gridDim.x * blockDim.x)
-        s += __bfloat162float(dY[(size_t)p * c + ch]);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(db + ch, s);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= G; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane < G)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) red[warp][8 * lane + k] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        atomicAdd(db + threadIdx.x, s);
+    }
 }
 
 // input layer: the FP32 input as channel 0 of a 16-channel BF16 volume, the n_aux medium
@@ -1421,8 +1436,16 @@ static mcx_status conv_bwd(mcx_denoiser *d, int l, const bf16 *in, Vol v, bf16 *
     const LayerSpec &L = kLayers[l];
     float *G = d->grads.as<float>();
     bf16 *dA = d->ga[l].as<bf16>();
-    relu_mask<<<grid1(v.pos() * L.cout / 8), 256, 0, st>>>(dA, d->a[l].as<bf16>(), (int)(v.pos() * L.cout / 8));
-    bias_grad<<<dim3(64, L.cout), 256, 0, st>>>(dA, (int)v.pos(), L.cout, G + d->b_off[l]);
+    const int n8 = (int)(v.pos() * L.cout / 8);
+    const unsigned rb = std::min(grid1(n8), 152u * 4u);
+    const bf16 *A = d->a[l].as<bf16>();
+    float *db = G + d->b_off[l];
+    switch (L.cout) {
+    case 16: relu_bias_grad<16><<<rb, 256, 0, st>>>(dA, A, n8, db); break;
+    case 32: relu_bias_grad<32><<<rb, 256, 0, st>>>(dA, A, n8, db); break;
+    case 64: relu_bias_grad<64><<<rb, 256, 0, st>>>(dA, A, n8, db); break;
+    default: return dn_fail(d, MCX_E_STATE, "no ReLU/bias-gradient kernel for this channel count");
+    }
     DNC(d, launch_bwd_w(in, L.cin, dA, L.cout, v, G + d->w_off[l], d->status.as<unsigned>(), st), "weight gradient");
     if (dIn)
         DNC(d, launch_fwd_tc(dA, L.cout, d->wb[l].as<bf16>(), nullptr, v, L.cin, 0, dIn, d->status.as<unsigned>(), st),
