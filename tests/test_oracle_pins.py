@@ -248,6 +248,30 @@ def test_beer_lambert_column_exact(orc, h):
     assert np.allclose(r.exits["t"], nz * h * n / C0, rtol=1e-12)
 
 
+def test_ballistic_transmission_through_two_scattering_layers(orc):
+    """Index-matched two-layer slab (no Fresnel events): a photon leaves through the far
+    face unscattered with probability exp(-(mus1 L1 + mus2 L2)), since its hop length in
+    mean free paths is exponential and is spent at each layer's own mus; such a photon
+    exits on the beam axis at t = L n / c0 with weight exp(-(mua1 L1 + mua2 L2))."""
+    n, N = 1.0, 20000
+    mus, mua, L = (0.2, 0.1), (0.01, 0.02), (5, 5)
+    wl = _slab(40, 40, sum(L), [(0, 0, 1, n), (mua[0], mus[0], 0.9, n), (mua[1], mus[1], 0.5, n)],
+               n_photons=N, src_pos=(20.0, 20.0, 0.0))
+    wl.labels[L[0]:] = 2
+    r = orc.run(wl, exit_cap=N)
+    ex = r.exits
+    ballistic = ex[ex["nscat"] == 0]
+    assert np.all(ballistic["fate"] == orc.FATE_ESCAPED)
+    p = math.exp(-(mus[0] * L[0] + mus[1] * L[1]))
+    sigma = math.sqrt(p * (1 - p) / N)
+    assert abs(len(ballistic) / N - p) < 4 * sigma
+    assert np.allclose(ballistic["pos"], [20.0, 20.0, sum(L)], atol=1e-12)
+    assert np.allclose(ballistic["dir"], [0.0, 0.0, 1.0], atol=1e-12)
+    assert np.allclose(ballistic["w"], math.exp(-(mua[0] * L[0] + mua[1] * L[1])), rtol=1e-12)
+    assert np.allclose(ballistic["t"], sum(L) * n / C0, rtol=1e-12)
+    assert np.all(ex["nscat"][ex["pos"][:, 2] < sum(L) - 1e-9] > 0)   # the rest scattered
+
+
 def test_time_limit_stops_photon_at_ct(orc):
     n = 1.37
     wl = _slab(8, 8, 200, [(0, 0, 1, n), (0.0, 0.0, 0.0, n)], n_photons=10, n_gates=4,
