@@ -86,9 +86,11 @@ struct Vol {
 // and commits to "empty" (the stage may be refilled) and, after a tile's last window, to
 // "acc full"; warps 2-5 read the accumulator out (tcgen05.ld; warp w reads TMEM lanes
 // 32 (w mod 4) ...), arrive on "acc empty", and store bias + ReLU in BF16 for the valid
-// rows.  Two TMEM accumulators let a tile's read-out overlap the next tile's MMAs.  The
-// layer's weights stay resident in shared memory when they fit (one TMA load each), else
-// each stage also carries its plane's 9 taps of weights.
+// rows.  Several TMEM accumulators let a tile's read-out overlap the next tiles' MMAs.
+// The layer's weights stay resident in shared memory when they fit (one TMA load each).
+// With cout = 16 or 32 the three tiles a window feeds sit in consecutive accumulators and
+// take one MMA of N = 3 cout per (dy, dx) tap and K step (two where the accumulator ring
+// wraps), so the window's A rows are read from shared memory once instead of three times.
 //
 // Every wait is bounded: on a timeout the role records an error and stops; the CTA still
 // waits (bounded) for its TMA loads and frees its tensor memory.
@@ -128,13 +130,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int kTcRows = 128, kTcThreads = 192, kTcHeader = 256;
+constexpr int kTcRows = 128, kTcThreads = 192, kTcHeader = 256, kTcFwdHeader = 384;
 constexpr int kTcWallMax = 64 * 1024;       // weights up to this size stay resident
 constexpr int kTcSmemBudget = 112 * 1024;   // preferred shared memory per CTA
 constexpr int kTcSmemMax = 227 * 1024;      // shared memory one CTA may use
 constexpr int kTcMaxStages = 8;
 
 __host__ __device__ constexpr bool tc_wall(int cin, int cout) { return 27 * cin * cout * 2 <= kTcWallMax; }
+// resident weights and cout 16 or 32: one window's products for its (up to) three tiles
+// go out as one MMA with N = tiles x cout (weights stored dz-interleaved per (dy, dx) tap)
+__host__ __device__ constexpr bool tc_merge(int cin, int cout) { return tc_wall(cin, cout) && (cout == 16 || cout == 32); }
+// TMEM columns per accumulator and accumulators per CTA (128 columns or fewer with
+// resident weights, so four CTAs fit an SM's 512)
+__host__ __device__ constexpr int tc_ncol(int cin, int cout)
+{
+    return tc_merge(cin, cout) ? cout : (cout <= 32 ? 32 : (cout <= 64 ? 64 : 128));
+}
+__host__ __device__ constexpr int tc_nslot(int cin, int cout)
+{
+    return tc_merge(cin, cout) ? (cout == 16 ? 8 : 4) : (tc_wall(cin, cout) ? 4 : 2);
+}
 // lines of a window: the tile's rows q0 - 1 - PW .. q0 + 128 + PW
 __host__ __device__ constexpr int tc_lines(int w) { return (kTcRows + 2 + w + 1) / (w + 2) + 3; }
 // one 8-channel chunk of a window: L lines x PW rows of 16 B, padded to 128 B
@@ -145,7 +160,7 @@ __host__ __device__ constexpr int tc_stage_bytes(int cin, int cout, int w)
 }
 __host__ __device__ constexpr int tc_smem_bytes(int cin, int cout, int w, int ns)
 {
-    return 1024 + kTcHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + ns * tc_stage_bytes(cin, cout, w);
+    return 1024 + kTcFwdHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + ns * tc_stage_bytes(cin, cout, w);
 }
 // ring depth: each CTA has one MMA-issuing thread, so more resident CTAs issue more
 // MMAs; prefer 3-8 stages within a quarter of the SM's shared memory (4 CTAs), then 2-8
@@ -217,21 +232,26 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
 {
     constexpr int cin = CIN;
     constexpr bool WALL = tc_wall(CIN, COUT);
-    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);   // TMEM columns per accumulator
-    constexpr int NSLOT = WALL ? 4 : 2;                                // accumulators per CTA
+    constexpr bool MERGE = tc_merge(CIN, COUT);
+    constexpr int NCOL = tc_ncol(CIN, COUT);                           // TMEM columns per accumulator
+    constexpr int NSLOT = tc_nslot(CIN, COUT);                         // accumulators per CTA
     constexpr uint32_t IDESC = idesc_bf16_f32(kTcRows, COUT);
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
-    // header: full[ns] at 0, empty[ns] at 64, acc full[4] at 128, acc empty[4] at 160,
-    // weights barrier at 192, TMEM address at 224
-    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 160, wbar = base + 192;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 224 - smem_u32(smem_raw)));
+    // header: full[ns] at 0, empty[ns] at 64, acc full[NSLOT] at 128, acc empty[NSLOT] at
+    // 192, weights barrier at 256, TMEM address at 320
+    const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 192, wbar = base + 256;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 320 - smem_u32(smem_raw)));
     const int wtap = COUT * cin * 2, lbo_b = COUT * 16;
     const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
     const int a_bytes = (cin / 8) * lbo_a;
-    const uint32_t wres = base + kTcHeader;
+    const uint32_t wres = base + kTcFwdHeader;
     const uint32_t ring = wres + (WALL ? 27 * wtap : 0);
     const int stage_bytes = a_bytes + (WALL ? 0 : 9 * wtap);
+    // merged weights: per (dy, dx) tap tt and 8-channel chunk c, the rows of dz = +1, 0, -1
+    // (cout each, 16 B per row) one after another, so the tiles w - 1, w, w + 1 that a
+    // window of plane w feeds are consecutive N rows; chunks LBOM bytes apart
+    constexpr int LBOM = 3 * COUT * 16;
     const int tid = threadIdx.x, warp = tid >> 5;
     // work units: columns of up to zc tiles at the same q0 in consecutive planes
     const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
@@ -278,8 +298,12 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
         if (WALL && my_units) {
             mbar_expect_tx(wbar, 27 * wtap);
             for (int tap = 0; tap < 27; ++tap)
-                for (int c = 0; c < cin / 8; ++c)
-                    tma_load_2d(wres + tap * wtap + c * lbo_b, &tmw, 8 * c, tap * COUT, wbar);
+                for (int c = 0; c < cin / 8; ++c) {
+                    const int tt = tap % 9, dzi = 2 - tap / 9;    // dzi = 1 - dz
+                    const uint32_t dst = MERGE ? wres + tt * 3 * wtap + c * LBOM + dzi * COUT * 16
+                                               : wres + tap * wtap + c * lbo_b;
+                    tma_load_2d(dst, &tmw, 8 * c, tap * COUT, wbar);
+                }
         }
         const uint32_t tx = a_bytes / lbo_a * (L * PW * 16) + (WALL ? 0 : 9 * wtap);
         int b = 0, use = 0;
@@ -325,6 +349,47 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 // descriptors differ only in the start-address field (address / 16, 14 bits;
                 // every address here is below 256 KiB): base descriptor plus an offset
                 const uint64_t abase = adesc0 + (uint64_t)((b * stage_bytes + off * 16) >> 4);
+                if constexpr (MERGE) {
+                    // tiles ilo .. ihi read this plane (tile i with dz = j - 1 - i, weight block
+                    // dzi = i - j + 2); tile j starts here, tile j - 2 finishes here
+                    const int ilo = max(0, j - 2), ihi = min(U.nz - 1, j);
+                    const bool starts = ihi == j;
+                    if (starts && T0 + j >= NSLOT) {            // the slot's previous tile is read out
+                        ok &= mbar_wait(acce0 + 8 * ((T0 + j) & (NSLOT - 1)), (uint32_t)(((T0 + j) / NSLOT - 1) & 1));
+                        tc_fence_after();
+                    }
+                    if (!ok) break;
+                    const uint64_t bdm = umma_desc(wres, LBOM, 128);
+                    // one MMA for tiles a .. e (consecutive accumulators, no wrap of the ring)
+                    auto mma_run = [&](uint64_t ad, uint64_t bk, int a, int e, uint32_t accum) {
+                        const uint32_t d = tmem + (uint32_t)(((T0 + a) & (NSLOT - 1)) * NCOL);
+                        const uint64_t bd = bk + (uint64_t)(((a - j + 2) * COUT * 16) >> 4);
+                        const uint32_t idesc = idesc_bf16_f32(kTcRows, (e - a + 1) * COUT);
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                     ::"r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+                    };
+#pragma unroll
+                    for (int tt = 0; tt < 9; ++tt)
+#pragma unroll
+                        for (int kk = 0; kk < CIN / 16; ++kk) {
+                            const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                            const uint64_t bk = bdm + (uint64_t)((tt * 3 * wtap + 2 * kk * LBOM) >> 4);
+                            // the starting tile's first product overwrites its accumulator
+                            const bool fresh = starts && tt == 0 && kk == 0;
+                            const int last = fresh ? j - 1 : ihi;
+                            for (int a = ilo; a <= last;) {
+                                const int e = min(last, a + (NSLOT - 1) - ((T0 + a) & (NSLOT - 1)));
+                                mma_run(ad, bk, a, e, 1u);
+                                a = e + 1;
+                            }
+                            if (fresh) mma_run(ad, bk, j, j, 0u);
+                        }
+                    if (j >= 2) tc_commit(accf0 + 8 * ((T0 + j - 2) & (NSLOT - 1)));   // tile j - 2 is complete
+                    tc_commit(empty0 + 8 * b);
+                    if (++b == ns) { b = 0; ++use; }
+                    continue;
+                }
                 // tiles i of the unit reading this plane, the finishing one first: dz = j - 1 - i
                 for (int i = j - 2; i <= j; ++i) {
                     if (i < 0 || i >= U.nz) continue;
@@ -1228,15 +1293,14 @@ cudaError_t launch_tc_t(const bf16 *X, const bf16 *W, const float *bias, Vol v, 
     cudaError_t e = cudaFuncSetAttribute(conv3d_fwd_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // resident CTAs per SM: shared memory (1 KiB per CTA reserved by the system), tensor
-    // memory (512 columns, two accumulators per CTA), threads
+    // memory (512 columns, NSLOT accumulators per CTA), threads
     int dev = 0, sms = 0, smem_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
         return e;
-    constexpr int ncol = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
-    constexpr int nslot = tc_wall(CIN, COUT) ? 4 : 2;
-    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / (nslot * ncol), 2048 / kTcThreads}));
+    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / (tc_nslot(CIN, COUT) * tc_ncol(CIN, COUT)),
+                                             2048 / kTcThreads}));
     const long long tiles_plane = (v.h * (v.w + 2) + kTcRows - 1) / kTcRows;
     if ((long long)v.n * v.d * tiles_plane * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
     // column depth: the deepest of 16, 8, 4, 2 that still leaves 3 units per resident CTA
