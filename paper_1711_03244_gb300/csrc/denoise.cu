@@ -88,9 +88,9 @@ struct Vol {
 // 32 (w mod 4) ...), arrive on "acc empty", and store bias + ReLU in BF16 for the valid
 // rows.  Several TMEM accumulators let a tile's read-out overlap the next tiles' MMAs.
 // The layer's weights stay resident in shared memory when they fit (one TMA load each).
-// With cout = 16 or 32 the three tiles a window feeds sit in consecutive accumulators and
-// take one MMA of N = 3 cout per (dy, dx) tap and K step (two where the accumulator ring
-// wraps), so the window's A rows are read from shared memory once instead of three times.
+// With cout = 16 the three tiles a window feeds sit in consecutive accumulators and take
+// one MMA of N = 48 per (dy, dx) tap and K step (two where the accumulator ring wraps), so
+// the window's A rows are read from shared memory once instead of three times.
 //
 // Every wait is bounded: on a timeout the role records an error and stops; the CTA still
 // waits (bounded) for its TMA loads and frees its tensor memory.
@@ -137,18 +137,20 @@ constexpr int kTcSmemMax = 227 * 1024;      // shared memory one CTA may use
 constexpr int kTcMaxStages = 8;
 
 __host__ __device__ constexpr bool tc_wall(int cin, int cout) { return 27 * cin * cout * 2 <= kTcWallMax; }
-// resident weights and cout 16 or 32: one window's products for its (up to) three tiles
-// go out as one MMA with N = tiles x cout (weights stored dz-interleaved per (dy, dx) tap)
-__host__ __device__ constexpr bool tc_merge(int cin, int cout) { return tc_wall(cin, cout) && (cout == 16 || cout == 32); }
-// TMEM columns per accumulator and accumulators per CTA (128 columns or fewer with
-// resident weights, so four CTAs fit an SM's 512)
+// resident weights and cout 16: one window's products for its (up to) three tiles go out
+// as one MMA with N = tiles x cout (weights stored dz-interleaved per (dy, dx) tap).  With
+// cout 32 the same scheme measured slower (four accumulators: the MMA thread waits for
+// read-outs, since a tile completes only with the whole window's MMAs)
+__host__ __device__ constexpr bool tc_merge(int cin, int cout) { return tc_wall(cin, cout) && cout == 16; }
+// TMEM columns per accumulator and accumulators per CTA (the launch counts their product
+// against an SM's 512 columns when it sizes the grid)
 __host__ __device__ constexpr int tc_ncol(int cin, int cout)
 {
     return tc_merge(cin, cout) ? cout : (cout <= 32 ? 32 : (cout <= 64 ? 64 : 128));
 }
 __host__ __device__ constexpr int tc_nslot(int cin, int cout)
 {
-    return tc_merge(cin, cout) ? (cout == 16 ? 8 : 4) : (tc_wall(cin, cout) ? 4 : 2);
+    return tc_merge(cin, cout) ? 8 : (tc_wall(cin, cout) ? 4 : 2);
 }
 // lines of a window: the tile's rows q0 - 1 - PW .. q0 + 128 + PW
 __host__ __device__ constexpr int tc_lines(int w) { return (kTcRows + 2 + w + 1) / (w + 2) + 3; }
