@@ -320,6 +320,33 @@ def test_fresnel_slab_with_absorption(orc):
     assert np.all((np.round(k) % 2 == 1) == (ex["pos"][:, 2] == D))
 
 
+def test_total_internal_reflection_traps_a_ray(orc):
+    """Non-scattering cube of n = 1.37 in air, ray along (1, 1, 1)/sqrt 3: every direction
+    cosine (0.577) is below cos(critical angle) = sqrt(1 - 1/1.37^2) = 0.683, so each face
+    reflects it totally and it never escapes.  It runs until the time limit, c0 T / n
+    of path, and stops where the mirror images of the straight ray put it (each
+    reflection flips one component); its weight is exp(-mua L), the rest absorbed."""
+    n, mua, side, T = 1.37, 0.01, 10, 0.3
+    u = 1.0 / math.sqrt(3.0)
+    wl = _slab(side, side, side, [(0, 0, 1, 1.0), (mua, 0.0, 0.0, n)], src_pos=(3.0, 4.0, 0.0),
+               src_dir=(u, u, u), n_photons=3, n_gates=1, dt_ns=T)
+    r = orc.run(wl, exit_cap=3)
+    L = C0 * T / n
+    s = L * u
+    def fold(x):                     # mirror images of [0, side]
+        x = math.fmod(x, 2 * side)
+        return 2 * side - x if x > side else x
+    expect = [fold(3.0 + s), fold(4.0 + s), fold(s)]
+    assert np.all(r.exits["fate"] == orc.FATE_TIME)
+    assert np.allclose(r.exits["pos"], expect, atol=1e-9)
+    assert np.allclose(np.abs(r.exits["dir"]), u, atol=1e-12)
+    assert np.allclose(r.exits["w"], math.exp(-mua * L), rtol=1e-12)
+    assert np.allclose(r.exits["t"], T, rtol=1e-12)
+    assert r.tally["escaped"] == 0.0
+    assert abs(r.tally["time_exceeded"] - 3 * math.exp(-mua * L)) < 1e-12
+    assert abs(r.energy.sum() - 3 * (1 - math.exp(-mua * L))) < 1e-12
+
+
 def test_snell_refraction_on_ballistic_ray(orc):
     """Oblique non-scattering ray through an n=1.0 | n=1.5 interface at z = 8 mm, with the
     exterior matched to the lower layer: every bottom exit lies where Snell's law puts it
