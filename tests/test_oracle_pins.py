@@ -446,6 +446,35 @@ def test_detector_weight_identity(orc):
         assert np.all(L >= 0) and np.all(rec[:, 2] >= 1)
 
 
+def test_detector_membership_and_tie_break(orc):
+    """A photon is detected exactly when it escapes through a face at a point within a
+    detector's radius (3-D distance to the centre); where disks overlap the lowest id
+    takes it.  Checked against the exit log of every photon, with two overlapping
+    disks on the entry face and disks on two side faces."""
+    import dataclasses
+    labels = np.ones((16, 16, 16), dtype=np.uint8)
+    det = np.array([[7.0, 8.0, 0.0, 2.5], [9.0, 8.0, 0.0, 2.5], [16.0, 8.0, 8.0, 3.0],
+                    [8.0, 16.0, 4.0, 2.0]])
+    N = 5000
+    wl = dataclasses.replace(workloads.c1(n_photons=N), labels=labels,
+                             media=np.array([(0, 0, 1, 1.0), (0.01, 2.0, 0.8, 1.37)]),
+                             src_pos=(8.0, 8.0, 0.0), detectors=det, max_detected=N)
+    r = orc.run(wl, exit_cap=N)
+    ex = r.exits
+    expect = {}
+    for pid in np.nonzero(ex["fate"] == orc.FATE_ESCAPED)[0]:
+        d2 = ((det[:, :3] - ex["pos"][pid]) ** 2).sum(axis=1)
+        hit = np.nonzero(d2 <= det[:, 3] ** 2)[0]
+        if hit.size:
+            expect[int(pid)] = int(hit[0])
+    got = {int(p): int(d) for p, d in zip(r.det_rec[:, 0], r.det_rec[:, 1])}
+    assert got == expect
+    assert len(set(expect.values())) == 4              # every disk, the overlap included, sees photons
+    both = [p for p, d in expect.items()
+            if d == 0 and ((ex["pos"][p][:3] - det[1, :3]) ** 2).sum() <= det[1, 3] ** 2]
+    assert len(both) > 10                              # photons in the overlap went to id 0
+
+
 def test_roulette_survival_fraction(orc):
     """Survivors carry m w: the killed weight is (m - 1) times the pre-roulette weight of
     the survivors on average, i.e. killed ~= gained."""
