@@ -272,6 +272,31 @@ def test_ballistic_transmission_through_two_scattering_layers(orc):
     assert np.all(ex["nscat"][ex["pos"][:, 2] < sum(L) - 1e-9] > 0)   # the rest scattered
 
 
+def test_time_gates_are_causal(orc):
+    """A deposit made in voxel v at time t needs a path of at least the distance d(v)
+    from the source to v's box, travelled at c0 / n, so gate g = floor(t / dt) of
+    voxel v stays empty for g < floor(d(v) n / (c0 dt)); the early gates near the beam do
+    receive deposits."""
+    import dataclasses
+    dt, G, n = 0.02, 25, 1.37
+    wl = dataclasses.replace(workloads.c1(n_photons=3000), n_gates=G, dt_ns=dt)
+    r = orc.run(wl)
+    E = r.energy
+    nz, ny, nx = wl.labels.shape
+    src = np.array(wl.src_pos)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    lo = np.stack([i, j, k], axis=-1).astype(float)
+    gap = np.maximum(0.0, np.maximum(lo - src, src - (lo + 1.0)))
+    d = np.sqrt((gap ** 2).sum(axis=-1))
+    gmin = np.floor(d * n / (C0 * dt)).astype(int)
+    g = np.arange(G)[:, None, None, None]
+    early = g < gmin[None]
+    assert early.sum() > 0.5 * early.size / G         # the bound excludes many (gate, voxel) pairs
+    assert np.all(E[early] == 0.0)
+    # the deposits do reach into every gate, so the bound is not vacuous
+    assert np.all(E.reshape(G, -1).sum(axis=1) > 0)
+
+
 def test_time_limit_stops_photon_at_ct(orc):
     n = 1.37
     wl = _slab(8, 8, 200, [(0, 0, 1, n), (0.0, 0.0, 0.0, n)], n_photons=10, n_gates=4,
