@@ -668,6 +668,14 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"first {nc} photons of {WORKLOAD} (FP64 oracle, "
                                           f"{cores} OpenMP threads, {cpu_ms / 1e3:.1f} s)"}
+        # the same oracle on one thread, over the first nc / cores of those photons
+        n1 = max(nc // cores, 1000)
+        t0 = time.perf_counter()
+        oracle.run(wl, n_photons=n1, energy=True, n_threads=1)
+        one_ms = 1e3 * (time.perf_counter() - t0)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": n1 / one_ms, "unit": UNIT, "cores": 1,
+            "sample": f"first {n1} photons of {WORKLOAD}, 1 thread, {one_ms / 1e3:.1f} s"}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
