@@ -297,6 +297,30 @@ def test_time_gates_are_causal(orc):
     assert np.all(E.reshape(G, -1).sum(axis=1) > 0)
 
 
+def test_diagonal_ray_through_voxel_edges(orc):
+    """A non-scattering ray from a voxel centre along (1, 1, 0)/sqrt 2 meets an x face and a
+    y face at once at every voxel edge (a tie, taken x first).  The step between the two
+    crossings has zero length, so all absorption lands on the diagonal voxels:
+    voxel (i, i) absorbs exp(-mua s_i) - exp(-mua s_i+1) with s_0 = 0 and
+    s_i = (i - 1/2) sqrt 2, and the ray leaves at the far edge."""
+    n_side, mua = 12, 0.05
+    u = 1.0 / math.sqrt(2.0)
+    labels = np.ones((5, n_side, n_side), dtype=np.uint8)
+    wl = _slab(n_side, n_side, 5, [(0, 0, 1, 1.0), (mua, 0.0, 0.0, 1.0)], labels=labels,
+               src_pos=(0.5, 0.5, 2.5), src_dir=(u, u, 0.0), n_photons=4)
+    r = orc.run(wl, exit_cap=4)
+    E = r.energy[0, 2] / wl.n_photons
+    s = np.array([0.0] + [(i + 0.5) * math.sqrt(2.0) for i in range(n_side)])
+    expect = np.zeros((n_side, n_side))
+    for i in range(n_side):
+        expect[i, i] = math.exp(-mua * s[i]) - math.exp(-mua * s[i + 1])
+    assert np.allclose(E, expect, rtol=1e-9, atol=1e-12)
+    assert abs(r.energy.sum() / wl.n_photons - (1 - math.exp(-mua * s[-1]))) < 1e-12
+    assert np.all(r.exits["fate"] == orc.FATE_ESCAPED)
+    assert np.allclose(r.exits["pos"], [n_side, n_side, 2.5], atol=1e-9)
+    assert np.allclose(r.exits["w"], math.exp(-mua * s[-1]), rtol=1e-12)
+
+
 def test_time_limit_stops_photon_at_ct(orc):
     n = 1.37
     wl = _slab(8, 8, 200, [(0, 0, 1, n), (0.0, 0.0, 0.0, n)], n_photons=10, n_gates=4,
