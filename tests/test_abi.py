@@ -72,6 +72,44 @@ def test_argument_errors_before_device_work(lib):
     L.mcx_destroy(None)
 
 
+def test_denoiser_and_batch_argument_errors(lib):
+    """The denoiser's shape limits and every NULL handle are rejected with MCX_E_ARG
+    before any device work, leaving the output handle NULL."""
+    m, L = lib
+    d = ctypes.c_void_p()
+    assert L.mcx_denoiser_create(None, 64, 64, 64, 1, 0, 0) == m.MCX_E_ARG
+    for nx, ny, nz, batch, n_aux in [(60, 64, 64, 1, 0), (256, 64, 64, 1, 0), (64, 6, 64, 1, 0),
+                                     (64, 64, 2, 1, 0), (64, 64, 64, 0, 0), (64, 64, 64, 1, 8),
+                                     (192, 252, 252, 64, 0)]:
+        d.value = None
+        assert L.mcx_denoiser_create(ctypes.byref(d), nx, ny, nz, batch, n_aux, 0) == m.MCX_E_ARG
+        assert not d.value
+    n = ctypes.c_uint64()
+    assert L.mcx_denoiser_param_count(None, ctypes.byref(n)) == m.MCX_E_ARG
+    assert L.mcx_denoiser_get_params(None, None, 0, 0) == m.MCX_E_ARG
+    assert L.mcx_denoiser_set_params(None, None, 0) == m.MCX_E_ARG
+    assert L.mcx_denoiser_set_encoding(None, 1e-8, -4.0, 2.0) == m.MCX_E_ARG
+    assert L.mcx_denoiser_forward(None, None, None, None, 1, None) == m.MCX_E_ARG
+    loss = ctypes.c_float()
+    assert L.mcx_denoiser_train_step(None, None, None, None, 1, 1e-3, ctypes.byref(loss), None) == m.MCX_E_ARG
+    assert L.mcx_denoiser_encode(None, None, None, 0, None) == m.MCX_E_ARG
+    assert L.mcx_denoiser_decode(None, None, None, 0, None) == m.MCX_E_ARG
+    assert L.mcx_denoiser_apply(None, None, None, None, 1, None) == m.MCX_E_ARG
+    assert L.mcx_denoiser_sync(None) == m.MCX_E_ARG
+    L.mcx_denoiser_destroy(None)
+    assert L.mcx_batch_create(None) == m.MCX_E_ARG
+    assert L.mcx_batch_run(None, None) == m.MCX_E_ARG
+    assert L.mcx_batch_sync(None) == m.MCX_E_ARG
+    ms = ctypes.c_float()
+    assert L.mcx_batch_last_ms(None, ctypes.byref(ms)) == m.MCX_E_ARG
+    assert L.mcx_batch_read_fluence(None, 0, None, 0, 0, 0) == m.MCX_E_ARG
+    assert L.mcx_batch_read_tally(None, 0, None) == m.MCX_E_ARG
+    assert L.mcx_batch_read_stats(None, None) == m.MCX_E_ARG
+    assert L.mcx_batch_autotune(None, None, 0.1, ctypes.byref(ms)) == m.MCX_E_ARG
+    assert L.mcx_batch_size(None) == 0
+    L.mcx_batch_destroy(None)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     import paper_1711_03244_gb300 as m
     saved = m._lib
