@@ -110,6 +110,25 @@ def test_denoiser_and_batch_argument_errors(lib):
     L.mcx_batch_destroy(None)
 
 
+def test_no_device_is_an_error_not_a_fallback(lib):
+    """Without a usable CUDA device every constructor fails with MCX_E_CUDA and leaves its
+    handle NULL: the library has no CPU path to fall back on."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    m, L = lib
+    h = ctypes.c_void_p()
+    lab = (ctypes.c_uint8 * 8)(*([1] * 8))
+    assert L.mcx_create_volume(ctypes.byref(h), 2, 2, 2, 1.0, lab, 0) == m.MCX_E_CUDA
+    assert not h.value and L.mcx_last_error(None)
+    b = ctypes.c_void_p()
+    assert L.mcx_batch_create(ctypes.byref(b)) == m.MCX_E_CUDA
+    assert not b.value
+    d = ctypes.c_void_p()
+    assert L.mcx_denoiser_create(ctypes.byref(d), 64, 64, 64, 1, 0, 0) == m.MCX_E_CUDA
+    assert not d.value
+
+
 def test_missing_library_fails_loudly(tmp_path):
     import paper_1711_03244_gb300 as m
     saved = m._lib
