@@ -1,6 +1,8 @@
 // Learned 3-D denoiser for low-photon fluence maps: a small U-Net (3 levels, 16/32/64
 // channels, 3x3x3 convolutions) with BF16 weights and activations and FP32 accumulation,
-// trained and run by hand-written tensor-core kernels (warp-level mma.sync m16n8k16).
+// trained and run by hand-written tensor-core kernels: the convolutions and their input
+// gradients on tcgen05 (TMA-fed shared-memory operands, accumulators in tensor memory),
+// the weight gradients on warp-level mma.sync m16n8k16.
 // The network stands in for photons: it maps the log-fluence of a low-photon run to the
 // log-fluence a high-photon run would give, and a plain high-photon run stays the
 // fallback.  (This extends the method; the paper has no counterpart.)
