@@ -8,15 +8,22 @@ generators, which hold none of the method's arithmetic).
 
 Parity status of each oracle function (what pins it, see tests/test_oracle_pins.py):
   * RNG (SplitMix64 seeding, xorshift128+ uniforms): SplitMix64 published test vector;
-    uniform moments, range and exact float representability; the pair and triple draws
-    against the bit fields of the single draws of the same outputs.
+    the xorshift128+ transition's full period 2^128 - 1 (its GF(2) matrix against the
+    prime factors of 2^128 - 1); uniform moments, range and exact float
+    representability; the pair and triple draws against the bit fields of the single
+    draws of the same outputs.
   * orc_hg_cos: mean cosine = g, chi^2 against the HG density, isotropic limit.
   * orc_rotate: unit norm, deflection cosine, azimuth uniformity, vertical special case.
   * orc_fresnel_R: normal-incidence closed form, the independent sine/tangent form of the
     Fresnel equations, critical angle, R + T = 1 with the transmission form.
-  * orc_run: Beer-Lambert column (exact), Fresnel slab escape series (binomial), exact
-    energy balance, detector weight identity, Snell refraction on a ballistic ray,
-    Gaussian-source moments, diffusion-theory far field (about 10%).
+  * orc_run: Beer-Lambert column (exact), ballistic transmission through two scattering
+    layers (binomial), a ray trapped by total internal reflection and a diagonal ray
+    through voxel edges (exact), causality of the time gates, Fresnel slab escape series
+    (binomial), exact energy balance, detector weight identity, detector membership and
+    tie-break, Snell refraction on a ballistic ray, Gaussian-source moments,
+    diffusion-theory far field (about 10%).
+tests/test_oracle_mutants.py plants one plausible slip at a time in a copy of
+mcx_oracle.c and checks that some pin fails on it.
 """
 from __future__ import annotations
 
@@ -30,7 +37,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mcx_oracle.c")
-_LIB = os.path.join(_HERE, "libmcx_oracle.so")
+# MCX_ORACLE_LIB: a library compiled elsewhere from a modified copy of mcx_oracle.c (the
+# mutation tests run the pins against such copies); build() then leaves it as it is
+_LIB_OVERRIDE = os.environ.get("MCX_ORACLE_LIB")
+_LIB = _LIB_OVERRIDE or os.path.join(_HERE, "libmcx_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -44,6 +54,8 @@ C0_MM_PER_NS = 299.792458
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP) next to its source."""
+    if _LIB_OVERRIDE:
+        return _LIB
     with _lock:
         if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
                 os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mcx_oracle.h"))):
@@ -123,6 +135,8 @@ def lib():
         L.orc_uniform_triples.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                         ctypes.c_void_p]
         L.orc_uniform_triples.restype = None
+        L.orc_xorshift_step.argtypes = [ctypes.c_void_p]
+        L.orc_xorshift_step.restype = None
         L.orc_hg_cos.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_hg_cos.restype = ctypes.c_double
         L.orc_rotate.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
@@ -159,6 +173,13 @@ def uniform_triples(seed: int, photon: int, n: int) -> np.ndarray:
     out = np.empty(3 * n, dtype=np.float64)
     lib().orc_uniform_triples(seed, photon, n, out.ctypes.data)
     return out.reshape(n, 3)
+
+
+def xorshift_step(s0: int, s1: int):
+    """the generator's state (s0, s1) after one transition"""
+    st = np.array([s0, s1], dtype=np.uint64)
+    lib().orc_xorshift_step(st.ctypes.data)
+    return int(st[0]), int(st[1])
 
 
 def hg_cos(g: float, xi: float) -> float:

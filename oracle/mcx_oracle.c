@@ -120,6 +120,16 @@ void orc_uniform_triples(uint64_t seed, uint64_t photon, uint64_t n, double *out
     for (uint64_t i = 0; i < n; ++i) rng_uniform_triple(&g, &out[3 * i], &out[3 * i + 1], &out[3 * i + 2]);
 }
 
+void orc_xorshift_step(uint64_t state[2])
+{
+    orc_rng g;
+    g.s0 = state[0];
+    g.s1 = state[1];
+    (void)rng_next(&g);
+    state[0] = g.s0;
+    state[1] = g.s1;
+}
+
 /* ------------------------------------------------------------------------------------
  * Henyey-Greenstein: inverse-CDF sample of the deflection cosine (Henyey & Greenstein
  * 1941; the closed-form inverse as used by MCML).  g = 0 is isotropic.

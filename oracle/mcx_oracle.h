@@ -97,6 +97,8 @@ uint64_t orc_splitmix64_output(uint64_t seed, uint64_t k);      /* k-th output, 
 void orc_uniforms(uint64_t seed, uint64_t photon, uint64_t n, double *out);
 void orc_uniform_pairs(uint64_t seed, uint64_t photon, uint64_t n, double *out);  /* 2n values */
 void orc_uniform_triples(uint64_t seed, uint64_t photon, uint64_t n, double *out);  /* 3n values */
+/* one xorshift128+ state transition of state[0..1] in place (the output is not formed) */
+void orc_xorshift_step(uint64_t state[2]);
 double orc_hg_cos(double g, double xi);
 void orc_rotate(const double u[3], double cos_t, double phi, double out[3]);
 double orc_fresnel_R(double n1, double n2, double cos_i);       /* returns 1 on TIR */

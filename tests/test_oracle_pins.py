@@ -33,6 +33,69 @@ def test_splitmix64_published_outputs(orc):
         assert orc.splitmix64_output(0, int(k)) == int(hexval, 16)
 
 
+def _is_prime(n):
+    """deterministic Miller-Rabin for n < 3.3e24"""
+    if n < 2:
+        return False
+    for p in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41):
+        if n % p == 0:
+            return n == p
+    d, r = n - 1, 0
+    while d % 2 == 0:
+        d, r = d // 2, r + 1
+    for a in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41):
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(r - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def test_xorshift128plus_transition_has_full_period(orc):
+    """The per-photon generator is xorshift128+ (shifts 23, 18, 5), whose state transition T
+    is linear over GF(2) and, for the published shift triple, has the maximal order
+    2^128 - 1: every nonzero state lies on one cycle.  T is read column by column from the
+    oracle's own transition (unit states in); its order is checked against the prime
+    factors of 2^128 - 1.  A wrong shift or operand in the transition breaks this."""
+    N = (1 << 128) - 1
+    primes = [3, 5, 17, 257, 641, 65537, 274177, 6700417, 67280421310721]
+    assert math.prod(primes) == N and all(_is_prime(p) for p in primes)
+
+    def step(v):
+        a, b = orc.xorshift_step(v & ((1 << 64) - 1), v >> 64)
+        return a | (b << 64)
+
+    cols = [step(1 << i) for i in range(128)]
+    rng = np.random.default_rng(3)
+    for _ in range(8):                                   # the transition is linear
+        u = int(rng.integers(0, 1 << 62)) | (int(rng.integers(0, 1 << 62)) << 64)
+        lin = 0
+        for i in range(128):
+            if (u >> i) & 1:
+                lin ^= cols[i]
+        assert step(u) == lin
+    T = np.array([[(c >> k) & 1 for c in cols] for k in range(128)], dtype=np.float32)
+    eye = np.eye(128, dtype=np.float32)
+
+    def power(M, e):
+        R, P = eye, M
+        while e:
+            if e & 1:
+                R = np.mod(R @ P, 2.0)
+            P = np.mod(P @ P, 2.0)
+            e >>= 1
+        return R
+
+    assert np.array_equal(power(T, N), eye)
+    for p in primes:
+        assert not np.array_equal(power(T, N // p), eye), p
+
+
 def test_uniforms_range_grid_and_moments(orc):
     u = np.concatenate([orc.uniforms(12345, p, 4096) for p in range(64)])
     assert u.min() > 0.0 and u.max() < 1.0
