@@ -21,11 +21,14 @@ Parity status (what pins each function, tests/test_denoiser_oracle.py):
   * conv3d: brute-force nested loops on tiny inputs; torch.nn.functional.conv3d.
   * avg_pool2 / upsample2: adjointness (<pool x, y> = <x, up y> / 8), constants.
   * forward: zero head returns the input; the one-layer case against brute force (with
-    and without feature channels); equivariance under shifts by 4 voxels away from the
-    boundary.
+    and without feature channels); the channel-0 pass-through network against its closed
+    form x + up(up(pool(pool(relu(x))))); equivariance under shifts by 4 voxels away from
+    the boundary.
   * features: hand-computed values for a two-label table and the exterior.
   * loss_and_grads: central finite differences of the exact FP64 loss.
   * adam: the closed form of the first step (|update| = lr for non-zero gradients).
+tests/test_denoiser_oracle_mutants.py plants one plausible slip at a time in a copy of
+this module and checks that some pin fails on it.
 """
 from __future__ import annotations
 

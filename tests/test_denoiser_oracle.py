@@ -104,6 +104,30 @@ def test_zero_head_returns_the_input():
     assert np.array_equal(y, x)
 
 
+def test_channel0_network_is_relu_pool_upsample():
+    """Every 3x3x3 convolution passes channel 0 through its centre tap (weight 1, no bias),
+    the head reads channel 0 with weight 1: the U-Net then computes exactly
+    y = x + up(up(pool(pool(relu(x))))) -- the first ReLU clips the input, later ones see
+    non-negative maps, each pooling averages 2x2x2 blocks, each upsampling repeats a voxel
+    2x2x2, and channel 0 of each concatenation is the upsampled path."""
+    flat = torch.zeros(od.param_count(), dtype=torch.float64)
+    p = od.unpack(flat)
+    for name in od.NAMES:
+        p[name + ".w"][13, 0, 0] = 1.0                   # tap 13 = (dz, dy, dx) = (0, 0, 0)
+    p["hw"][0] = 1.0
+    x = np.random.default_rng(9).normal(size=(1, 8, 8, 8))
+    y = od.forward(flat, x, bf16=False).numpy()
+
+    def pool(a):
+        n, D, H, W = a.shape
+        return a.reshape(n, D // 2, 2, H // 2, 2, W // 2, 2).mean(axis=(2, 4, 6))
+
+    def up(a):
+        return a.repeat(2, axis=1).repeat(2, axis=2).repeat(2, axis=3)
+
+    assert np.allclose(y, x + up(up(pool(pool(np.maximum(x, 0))))), rtol=0, atol=1e-12)
+
+
 def test_first_layer_against_brute_force():
     """the input layer sees the input as channel 0 of 16 zero-padded channels"""
     rng = np.random.default_rng(7)
