@@ -17,8 +17,9 @@ Parity status of each oracle function (what pins it, see tests/test_oracle_pins.
   * orc_fresnel_R: normal-incidence closed form, the independent sine/tangent form of the
     Fresnel equations, critical angle, R + T = 1 with the transmission form.
   * orc_run: Beer-Lambert column (exact), ballistic transmission through two scattering
-    layers (binomial), a ray trapped by total internal reflection and a diagonal ray
-    through voxel edges (exact), causality of the time gates, Fresnel slab escape series
+    layers (binomial), a ray trapped by total internal reflection, a diagonal ray
+    through voxel edges, the lowest-axis tie rule and a ray along x through two media
+    (exact), causality of the time gates, Fresnel slab escape series
     (binomial), exact energy balance, detector weight identity, detector membership and
     tie-break, Snell refraction on a ballistic ray, Gaussian-source moments,
     diffusion-theory far field (about 10%).

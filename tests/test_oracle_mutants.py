@@ -4,7 +4,7 @@ Each case plants one plausible mistake -- a dropped term, a wrong sign, index or
 transposed operand -- in a copy of oracle/mcx_oracle.c, compiles the copy to a library
 of its own, and runs tests/test_oracle_pins.py against it (MCX_ORACLE_LIB); at least
 one pin must fail (a pin that runs for more than 30 s counts as failing: some slips make
-a photon loop for ever).  The oracle's own source is never modified.  All cases run in
+a photon loop for ever; so does a crash, which an index slip can cause).  The oracle's own source is never modified.  All cases run in
 parallel subprocesses once per module.
 """
 import concurrent.futures
@@ -42,6 +42,18 @@ MUTANTS = [
     ("roulette survivors keep their weight", "w *= P->rr_m;", "(void)0;"),
     ("detector radius compared with the squared distance", "<= dd[3] * dd[3]", "<= dd[3]"),
     ("Gaussian radius without the 1/2", "sqrt(-log(xi1) / 2.0)", "sqrt(-log(xi1))"),
+    ("face ties taken on the highest axis", "if (d < d_face) { d_face = d; axis = a; bound = b; }",
+     "if (d <= d_face) { d_face = d; axis = a; bound = b; }"),
+    ("label lookup with x and y transposed",
+     "P->labels[((uint64_t)v[2] * P->ny + (uint64_t)v[1]) * P->nx + (uint64_t)v[0]]",
+     "P->labels[((uint64_t)v[2] * P->ny + (uint64_t)v[0]) * P->nx + (uint64_t)v[1]]"),
+    ("deposit index with x and y transposed",
+     "((uint64_t)v[2] * P->ny + (uint64_t)v[1]) * P->nx + (uint64_t)v[0];",
+     "((uint64_t)v[2] * P->ny + (uint64_t)v[0]) * P->nx + (uint64_t)v[1];"),
+    ("Fresnel reflectance without the 1/2", "return 0.5 * (rs * rs + rp * rp);", "return (rs * rs + rp * rp);"),
+    ("roulette gain counted as m w", "(P->rr_m - 1.0) * w;", "P->rr_m * w;"),
+    ("Snell: normal component reversed", "dir[axis] = dir[axis] > 0.0 ? cos_t : -cos_t;",
+     "dir[axis] = dir[axis] > 0.0 ? -cos_t : cos_t;"),
     ("triple draw: third uniform from the wrong bits", "(r >> 1) & 0x1FFFFFULL", "(r >> 2) & 0x1FFFFFULL"),
     ("xorshift128+: a shift constant", "a ^= a << 23;", "a ^= a << 22;"),
 ]
@@ -92,5 +104,7 @@ def test_a_pin_fails_on(outcomes, name):
     res = outcomes[name]
     assert not isinstance(res, str), res
     code, out = res
-    caught = " failed" in out or "Timeout" in out
-    assert code == 1 and caught, f"no pin failed (pytest exit {code}):\n{out}"
+    # a failing pin, a pin that never ends, or (an index slip reading outside the volume)
+    # the process killed by a signal
+    caught = (code == 1 and (" failed" in out or "Timeout" in out)) or code < 0
+    assert caught, f"no pin failed (pytest exit {code}):\n{out}"

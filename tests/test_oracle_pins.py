@@ -384,6 +384,45 @@ def test_diagonal_ray_through_voxel_edges(orc):
     assert np.allclose(r.exits["w"], math.exp(-mua * s[-1]), rtol=1e-12)
 
 
+def test_ray_along_x_through_two_media(orc):
+    """A non-scattering ray along +x at (y, z) = (12.5, 2.5) crosses 8 mm of mua1 and then
+    8 mm of mua2 (the media split at x = 8 mm, index matched): it leaves at x = 16 with
+    weight exp(-8 (mua1 + mua2)), and only the voxels of its row absorb, voxel x = i taking
+    its own exponential slice.  The geometry is not symmetric in x and y, so a transposed
+    label or deposit index fails it."""
+    mua1, mua2 = 0.02, 0.05
+    labels = np.ones((4, 16, 16), dtype=np.uint8)
+    labels[:, :, 8:] = 2
+    wl = _slab(16, 16, 4, [(0, 0, 1, 1.0), (mua1, 0.0, 0.0, 1.0), (mua2, 0.0, 0.0, 1.0)], labels=labels,
+               src_pos=(0.0, 12.5, 2.5), src_dir=(1.0, 0.0, 0.0), n_photons=3)
+    r = orc.run(wl, exit_cap=3)
+    mu = np.where(np.arange(16) < 8, mua1, mua2)
+    edges = np.concatenate([[0.0], np.cumsum(mu)])
+    expect = np.zeros((4, 16, 16))
+    expect[2, 12, :] = np.exp(-edges[:-1]) - np.exp(-edges[1:])
+    assert np.allclose(r.energy[0] / 3, expect, rtol=1e-12, atol=1e-15)
+    assert np.allclose(r.exits["pos"], [16.0, 12.5, 2.5], atol=1e-12)
+    assert np.allclose(r.exits["w"], math.exp(-8 * (mua1 + mua2)), rtol=1e-12)
+
+
+def test_face_tie_takes_the_lowest_axis(orc):
+    """Reading of the segment step: a tie between faces is taken on the lowest axis.  A
+    ray along (1, 1, 0)/sqrt 2 from the centre of voxel (0, 0) reaches its x and y faces at
+    once; the voxel across the x face is exterior (voxels with ix > iy are), the one across
+    the y face is not.  Taking x first, the photon escapes at that edge with the weight
+    of half a diagonal; taking y first it would run on to the far corner."""
+    n_side, mua = 8, 0.05
+    iy, ix = np.meshgrid(np.arange(n_side), np.arange(n_side), indexing="ij")
+    labels = np.repeat(np.where(ix > iy, 0, 1).astype(np.uint8)[None], 3, axis=0)
+    u = 1.0 / math.sqrt(2.0)
+    wl = _slab(n_side, n_side, 3, [(0, 0, 1, 1.0), (mua, 0.0, 0.0, 1.0)], labels=labels,
+               src_pos=(0.5, 0.5, 1.5), src_dir=(u, u, 0.0), n_photons=2)
+    r = orc.run(wl, exit_cap=2)
+    assert np.all(r.exits["fate"] == orc.FATE_ESCAPED)
+    assert np.allclose(r.exits["pos"], [1.0, 1.0, 1.5], atol=1e-12)
+    assert np.allclose(r.exits["w"], math.exp(-mua * math.sqrt(2.0) / 2), rtol=1e-12)
+
+
 def test_time_limit_stops_photon_at_ct(orc):
     n = 1.37
     wl = _slab(8, 8, 200, [(0, 0, 1, n), (0.0, 0.0, 0.0, n)], n_photons=10, n_gates=4,
