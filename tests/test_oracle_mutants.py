@@ -54,6 +54,10 @@ MUTANTS = [
     ("roulette gain counted as m w", "(P->rr_m - 1.0) * w;", "P->rr_m * w;"),
     ("Snell: normal component reversed", "dir[axis] = dir[axis] > 0.0 ? cos_t : -cos_t;",
      "dir[axis] = dir[axis] > 0.0 ? -cos_t : cos_t;"),
+    ("Gaussian azimuth over half a turn", "ph = 2.0 * ORC_PI * xi2;", "ph = ORC_PI * xi2;"),
+    ("launch on a face: the voxel behind", "if (c == (double)v[a] && dir[a] < 0.0) v[a] -= 1;",
+     "if (c == (double)v[a] && dir[a] > 0.0) v[a] -= 1;"),
+    ("detected record: paths shifted by one medium", "r[10 + m] = L[m];", "r[10 + m] = L[m - 1];"),
     ("triple draw: third uniform from the wrong bits", "(r >> 1) & 0x1FFFFFULL", "(r >> 2) & 0x1FFFFFULL"),
     ("xorshift128+: a shift constant", "a ^= a << 23;", "a ^= a << 22;"),
 ]
