@@ -9,7 +9,8 @@ generators, which hold none of the method's arithmetic).
 Parity status of each oracle function (what pins it, see tests/test_oracle_pins.py):
   * RNG (SplitMix64 seeding, xorshift128+ uniforms): SplitMix64 published test vector;
     the xorshift128+ transition's full period 2^128 - 1 (its GF(2) matrix against the
-    prime factors of 2^128 - 1); uniform moments, range and exact float
+    prime factors of 2^128 - 1); the sum scrambler's nonlinearity (linear complexity of
+    the top output bit); uniform moments, range and exact float
     representability; the pair and triple draws against the bit fields of the single
     draws of the same outputs.
   * orc_hg_cos: mean cosine = g, chi^2 against the HG density, isotropic limit.

@@ -60,6 +60,11 @@ MUTANTS = [
     ("detected record: paths shifted by one medium", "r[10 + m] = L[m];", "r[10 + m] = L[m - 1];"),
     ("triple draw: third uniform from the wrong bits", "(r >> 1) & 0x1FFFFFULL", "(r >> 2) & 0x1FFFFFULL"),
     ("xorshift128+: a shift constant", "a ^= a << 23;", "a ^= a << 22;"),
+    ("xorshift128+: output xor instead of sum", "const uint64_t result = a + b;", "const uint64_t result = a ^ b;"),
+    ("single draw: 2k instead of 2k + 1", "return (double)(2 * k + 1) * (1.0 / 16777216.0);",
+     "return (double)(2 * k) * (1.0 / 16777216.0);"),
+    ("pair draw: second uniform from the wrong bits", "*u2 = (double)(2 * ((r >> 18) & 0x7FFFFFULL) + 1)",
+     "*u2 = (double)(2 * ((r >> 17) & 0x7FFFFFULL) + 1)"),
 ]
 
 

@@ -96,6 +96,40 @@ def test_xorshift128plus_transition_has_full_period(orc):
         assert not np.array_equal(power(T, N // p), eye), p
 
 
+def _linear_complexity(bits):
+    """Berlekamp-Massey over GF(2): length of the shortest LFSR generating the bits"""
+    c, b, L, m = [1], [1], 0, 1
+    for i, s_i in enumerate(bits):
+        d = s_i
+        for j in range(1, L + 1):
+            d ^= c[j] & bits[i - j] if j < len(c) else 0
+        if d == 0:
+            m += 1
+            continue
+        t = c[:]
+        c = c + [0] * max(0, len(b) + m - len(c))
+        for j, bj in enumerate(b):
+            c[j + m] ^= bj
+        if 2 * L <= i:
+            L, b, m = i + 1 - L, t, 1
+        else:
+            m += 1
+    return L
+
+
+def test_xorshift128plus_output_adds_the_state_words(orc):
+    """xorshift128+ outputs the sum of its two state words mod 2^64.  The transition is
+    linear over GF(2), so any output bit of a linear scrambler (xor of the words, or one
+    word) would be an LFSR sequence of linear complexity at most 128; the carries of the
+    sum make the top bit nonlinear, and over 1000 draws its linear complexity comes out
+    near 500, as for a random sequence."""
+    u = orc.uniforms(12345, 7, 1000)
+    k = np.round((u * 2 ** 24 - 1) / 2).astype(np.int64)      # the top 23 output bits
+    top = [int(v >> 22) & 1 for v in k]
+    L = _linear_complexity(top)
+    assert 450 <= L <= 550, L
+
+
 def test_uniforms_range_grid_and_moments(orc):
     u = np.concatenate([orc.uniforms(12345, p, 4096) for p in range(64)])
     assert u.min() > 0.0 and u.max() < 1.0
