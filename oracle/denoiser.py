@@ -25,7 +25,8 @@ Parity status (what pins each function, tests/test_denoiser_oracle.py):
     form x + up(up(pool(pool(relu(x))))); equivariance under shifts by 4 voxels away from
     the boundary.
   * features: hand-computed values for a two-label table and the exterior.
-  * loss_and_grads: central finite differences of the exact FP64 loss.
+  * loss_and_grads: central finite differences of the exact FP64 loss; with the head's
+    weights at zero, the loss and its head-bias gradient in closed form.
   * adam: the closed form of the first step (|update| = lr for non-zero gradients).
 tests/test_denoiser_oracle_mutants.py plants one plausible slip at a time in a copy of
 this module and checks that some pin fails on it.

@@ -209,6 +209,22 @@ def test_gradients_against_finite_differences():
         assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9), i
 
 
+def test_loss_is_the_voxel_mean_with_its_closed_form_head_gradient():
+    """With the head's weights at zero the output is x + hb, so the loss
+    mean((x + hb - t)^2) and its gradient d/dhb = 2 mean(x + hb - t) follow in closed
+    form, while every other parameter's gradient is zero."""
+    rng = np.random.default_rng(11)
+    p = _random_params(rng, head=False)
+    p[-1] = 0.25                                        # hb
+    x = rng.normal(size=(2, 4, 4, 8))
+    t = rng.normal(size=(2, 4, 4, 8))
+    loss, g = od.loss_and_grads(p, x, t, bf16=False)
+    e = x + 0.25 - t
+    assert abs(loss - float(np.mean(e * e))) < 1e-12
+    assert abs(g[-1] - 2.0 * float(np.mean(e))) < 1e-12
+    assert np.all(g[:-17] == 0.0)                       # the head weights are zero
+
+
 def test_adam_first_step_closed_form():
     """with zero moments the first bias-corrected step moves each parameter by
     lr * g / (|g| + eps) ~ lr * sign(g)"""

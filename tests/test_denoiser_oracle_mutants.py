@@ -30,6 +30,7 @@ MUTANTS = [
     ("skip concatenated before the upsampled path", "torch.cat([upsample2(a7), a1], dim=-1)",
      "torch.cat([a1, upsample2(a7)], dim=-1)"),
     ("residual connection dropped", "return x + P[\"hb\"][0] + torch.einsum", "return P[\"hb\"][0] + torch.einsum"),
+    ("loss summed instead of averaged", "loss = ((y - tt) ** 2).mean()", "loss = ((y - tt) ** 2).sum()"),
     ("Adam without bias correction", "mh = m / (1 - b1 ** step)", "mh = m"),
     ("Adam: eps inside the square root", "(np.sqrt(vh) + eps)", "np.sqrt(vh + eps)"),
     ("encoding: sign of the offset", "- mu) / sigma", "+ mu) / sigma"),
