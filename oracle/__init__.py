@@ -24,6 +24,10 @@ Parity status of each oracle function (what pins it, see tests/test_oracle_pins.
     (binomial), exact energy balance, detector weight identity, detector membership and
     tie-break, Snell refraction on a ballistic ray, Gaussian-source moments,
     diffusion-theory far field (about 10%).
+  * normalise: hand-evaluated values of E / (mua h^3 N dt) (tests/golden/
+    normalised_fluence.txt) and, on an oracle run of a layered purely absorbing column,
+    the track-length estimate of the same fluence (the weight integrated numerically
+    along the path in each voxel, over h^3 dt).
 tests/test_oracle_mutants.py plants one plausible slip at a time in a copy of
 mcx_oracle.c and checks that some pin fails on it.
 """

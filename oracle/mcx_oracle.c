@@ -13,8 +13,16 @@
  *   refract / escape + detector), or scatter (Henyey-Greenstein + rotation with the next
  *   hop drawn alongside, then Russian roulette) }.
  *
- * Readings where the paper is silent are listed in the project's design notes; the main
- * ones are repeated at the place they apply.
+ * The paper defers the photon physics to the MCX/MCML formulation, so where it is silent
+ * this file takes these readings (each is repeated where it applies): voxel (i,j,k) covers
+ * [i h, (i+1) h) on each axis and label 0 or anything outside the grid is the exterior;
+ * the photon starts inside the medium with weight 1 and no specular loss; hops are in
+ * mean free paths, and the nearest of face, scattering point and time limit ends a
+ * segment (faces tie to the lowest axis, the time limit wins every tie); the deposit goes
+ * to the gate of the segment's start; unpolarised Fresnel reflectance with Snell
+ * refraction and total internal reflection; Russian roulette after each scattering event
+ * below w_min = 1e-4 with survival 1/m, m = 10; a detector takes an escaping photon whose
+ * exit point lies within its radius, the lowest id winning.
  */
 #include "mcx_oracle.h"
 

@@ -117,3 +117,40 @@ def test_a_pin_fails_on(outcomes, name):
     # the process killed by a signal
     caught = (code == 1 and (" failed" in out or "Timeout" in out)) or code < 0
     assert caught, f"no pin failed (pytest exit {code}):\n{out}"
+
+
+# Slips in the oracle's one Python-side arithmetic function, the fluence normalisation
+# E / (mua h^3 N dt): each mutant is compiled from the function's own source with one
+# expression changed, and the two normalisation pins run against it.
+NORMALISE_MUTANTS = [
+    ("voxel area instead of volume", "voxel_mm ** 3", "voxel_mm ** 2"),
+    ("gate width dropped", "n_photons * dt_ns)", "n_photons)"),
+    ("photon count dropped", "* n_photons * dt_ns", "* dt_ns"),
+    ("mua of the exterior row", "np.asarray(media)[:, 0][labels]", "np.asarray(media)[0, 0] + 0 * labels"),
+    ("mua = 0 voxels left undefined", "phi[:, mua == 0] = 0.0", "pass"),
+]
+
+
+@pytest.mark.parametrize("name, old, new", NORMALISE_MUTANTS, ids=[m[0] for m in NORMALISE_MUTANTS])
+def test_a_normalisation_pin_fails_on(orc, name, old, new):
+    import inspect
+    import types
+    import warnings
+    import numpy as np
+    sys.path.insert(0, os.path.dirname(PINS))
+    import test_oracle_pins as pins
+    src = inspect.getsource(orc.normalise)
+    assert src.count(old) == 1, (name, old)
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    fake = types.SimpleNamespace(**{k: getattr(orc, k) for k in dir(orc) if not k.startswith("__")})
+    fake.normalise = ns["normalise"]
+    failed = 0
+    for pin in (pins.test_normalised_fluence_golden, pins.test_normalised_fluence_is_the_track_length_fluence):
+        try:
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore")
+                pin(fake)
+        except AssertionError:
+            failed += 1
+    assert failed > 0, f"no normalisation pin failed on: {name}"

@@ -345,6 +345,56 @@ def test_beer_lambert_column_exact(orc, h):
     assert np.allclose(r.exits["t"], nz * h * n / C0, rtol=1e-12)
 
 
+def test_normalised_fluence_golden(orc):
+    """oracle.normalise on one voxel of known absorbed weight, mua, h, N and dt, against the
+    hand-evaluated values in tests/golden/normalised_fluence.txt."""
+    for E, mua, h, N, dt, phi in _read_golden("normalised_fluence.txt"):
+        E, mua, h, dt, phi = float(E), float(mua), float(h), float(dt), float(phi)
+        media = np.array([[0.0, 0.0, 1.0, 1.0], [mua, 1.0, 0.9, 1.37]])
+        labels = np.ones((1, 1, 1), dtype=np.uint8)
+        energy = np.array([[[[E]]]])
+        got = orc.normalise(energy, media, labels, h, int(N), dt)
+        assert got.shape == energy.shape
+        assert got[0, 0, 0, 0] == pytest.approx(phi, rel=1e-12, abs=0.0)
+
+
+def test_normalised_fluence_is_the_track_length_fluence(orc):
+    """In a purely absorbing layered column (index matched, pencil beam along +z, h = 0.5,
+    one gate of width dt), the normalised fluence of voxel k must equal the track-length
+    estimate of the same quantity: the photon weight integrated along the path inside the
+    voxel, w(z) = exp(-int_0^z mua), divided by the voxel volume h^3 and by dt (every photon
+    takes the same path, so the per-photon value does not depend on N).  The integral is
+    done numerically here (Simpson's rule), not by the absorption closed form.  Layers:
+    mua 0.05 (10 voxels), 0.2 (10 voxels), 0 (5 voxels, reported 0 by convention)."""
+    h, n, dt, N = 0.5, 1.37, 0.7, 13
+    mua = (0.0, 0.05, 0.2, 0.0)
+    nz = 25
+    wl = _slab(8, 8, nz, [(0, 0, 1, n), (mua[1], 0.0, 0.0, n), (mua[2], 0.0, 0.0, n),
+                          (mua[3], 0.0, 0.0, n)], voxel_mm=h, src_pos=(4 * h, 4 * h, 0.0),
+               n_photons=N, n_gates=1, dt_ns=dt)
+    wl.labels[10:20] = 2
+    wl.labels[20:] = 3
+    r = orc.run(wl)
+    phi = orc.normalise(r.energy, wl.media, wl.labels, h, N, dt)
+    lab = wl.labels[:, 4, 4]
+    mu_z = np.array([mua[v] for v in lab])
+
+    def weight(z):                      # exp(-optical depth) at depth z (mm)
+        k = np.minimum((z / h).astype(int), nz - 1)
+        full = np.concatenate([[0.0], np.cumsum(mu_z * h)])
+        return np.exp(-(full[k] + mu_z[k] * (z - k * h)))
+
+    for k in range(nz):
+        z = np.linspace(k * h, (k + 1) * h, 201)
+        wz = weight(z)
+        track = (z[1] - z[0]) / 3 * (wz[0] + wz[-1] + 4 * wz[1:-1:2].sum() + 2 * wz[2:-1:2].sum())
+        expect = track / (h ** 3 * dt) if mu_z[k] > 0 else 0.0
+        assert phi[0, k, 4, 4] == pytest.approx(expect, rel=1e-9, abs=1e-300), k
+    off_axis = phi.copy()
+    off_axis[0, :, 4, 4] = 0.0
+    assert np.all(off_axis == 0.0)
+
+
 def test_ballistic_transmission_through_two_scattering_layers(orc):
     """Index-matched two-layer slab (no Fresnel events): a photon leaves through the far
     face unscattered with probability exp(-(mus1 L1 + mus2 L2)), since its hop length in
