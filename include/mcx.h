@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define MCX_ABI_VERSION 1
+#define MCX_ABI_VERSION 2
 
 typedef struct mcx_sim mcx_sim;   /* opaque; owns all device buffers of one simulation */
 
@@ -296,25 +296,37 @@ void mcx_batch_destroy(mcx_batch *b);
      labels_dev   uint8 [nz][ny][nx] on the current device (read only)
      props        host float [n_media][4] as in mcx_set_media; 1 <= n_media <= 32
      src_kind, pos_mm, dir, waist_mm   as in mcx_set_source
-     cfg          as for mcx_run (cuda_stream honoured); needs accum_mode = 0 (FP32
-                  atomics into fluence_dev), precision = 0, exit_log = 0, max_detected = 0
-                  (no detectors), grid_size <= 2048
-     fluence_dev  float [n_gates][nz][ny][nx] on the current device; zeroed, then filled
-                  with absorbed weight (as mcx_read_fluence with normalized = 0)
-     tally_dev    double [MCX_NTALLY] on the current device, receives the energy tallies
+     cfg          as for mcx_run (cuda_stream honoured); needs precision = 0, exit_log = 0,
+                  max_detected = 0 (no detectors), grid_size <= 2048, and accum_mode
+                  0 (FP32 atomics: additions into a voxel that already holds more than about
+                  1e7 times their weight are lost, so a hot voxel's sum falls short by tens of
+                  percent at 1e8 photons) or 2 (FP64 atomics, exact to FP64 rounding)
+     fluence_dev  device memory of the current device holding n_gates*nz*ny*nx elements,
+                  float [n_gates][nz][ny][nx] for accum_mode 0, double for accum_mode 2;
+                  zeroed, then filled with absorbed weight (as mcx_read_fluence with
+                  normalized = 0).  The library cannot check its size: a smaller buffer is
+                  written past its end.
+     tally_dev    double [MCX_NOALLOC_NOUT] on the current device: the energy tallies
+                  (MCX_TALLY_*), then in word MCX_NTALLY the number of photons stopped by the
+                  per-photon event cap (their weight counted as time-exceeded).  A nonzero
+                  count is the condition mcx_sync reports as MCX_E_CAP for mcx_run: this
+                  call returns before the walk ends, so the caller reads it after
+                  synchronising the stream.
    Its working memory (photon counter, status, per-label tables, per-block partials) is a
    fixed 226 KiB array in the library, held by every GPU that loads it until the process
-   exits; sizes beyond its limits are rejected with MCX_E_ARG.  The first call on a device
-   looks up that array's device address; make that first call before any stream capture.
-   The call checks the labels (a 4-byte read-back that waits for the stream), then enqueues
-   the rest on cfg->cuda_stream and returns.  Every call reuses the same array: calls
-   whose work overlaps on one GPU (other streams or host threads) race on it; serialise
-   them.  Errors: MCX_E_ARG / MCX_E_STATE (a label >= n_media) / MCX_E_CUDA, described by
-   mcx_last_error(NULL). */
+   exits; sizes beyond its limits are rejected with MCX_E_ARG, as are pointers that are not
+   device memory of the current device.  The first call on a device looks up that array's
+   device address.  The call checks the labels (a 4-byte read-back that waits for the
+   stream), then enqueues the rest on cfg->cuda_stream and returns; because of that wait it
+   cannot be made while its stream is being captured into a CUDA graph (MCX_E_STATE).
+   Every call reuses the same array: calls whose work overlaps on one GPU (other streams or
+   host threads) race on it; serialise them.  Errors: MCX_E_ARG / MCX_E_STATE (a label >=
+   n_media, or stream capture) / MCX_E_CUDA, described by mcx_last_error(NULL). */
+#define MCX_NOALLOC_NOUT (MCX_NTALLY + 1)
 mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, uint32_t ny, uint32_t nz,
                            float voxel_mm, uint32_t n_media, const float *props,
                            int32_t src_kind, const float pos_mm[3], const float dir[3],
-                           float waist_mm, const mcx_run_cfg *cfg, float *fluence_dev,
+                           float waist_mm, const mcx_run_cfg *cfg, void *fluence_dev,
                            double *tally_dev);
 
 /* ---- learned denoiser -----------------------------------------------------------------

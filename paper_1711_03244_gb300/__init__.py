@@ -345,12 +345,37 @@ def mcx_destroy(sim):
         load().mcx_destroy(sim)
 
 
+NOALLOC_NOUT = 7        # tallies, then the count of photons stopped by the event cap
+
+
 def mcx_run_noalloc(labels_dev, voxel_mm: float, media, src_kind: int, pos, direction,
                     waist_mm: float, cfg: McxRunCfg, fluence_dev, tally_dev):
     """Allocation-free run on caller-owned device tensors (see include/mcx.h): labels_dev
-    uint8 [nz, ny, nx], fluence_dev float32 [n_gates, nz, ny, nx], tally_dev float64 [6],
-    all on the current CUDA device.  Enqueued on cfg.cuda_stream."""
-    nz, ny, nx = labels_dev.shape
+    uint8 [nz, ny, nx]; fluence_dev [n_gates, nz, ny, nx], float32 for accum_mode 0 and
+    float64 for accum_mode 2; tally_dev float64 [7] (the six tallies, then the number of
+    photons stopped by the per-photon event cap); all contiguous torch tensors on the
+    current CUDA device.  Enqueued on cfg.cuda_stream.  The tensors are checked here
+    before the library is called, since it cannot check a buffer's size."""
+    import torch
+    dev = torch.cuda.current_device()
+    expect = {"labels_dev": (labels_dev, torch.uint8, None),
+              "fluence_dev": (fluence_dev, torch.float64 if cfg.accum_mode == 2 else torch.float32,
+                              None),
+              "tally_dev": (tally_dev, torch.float64, NOALLOC_NOUT)}
+    if labels_dev is not None and getattr(labels_dev, "dim", lambda: 0)() == 3:
+        nz, ny, nx = labels_dev.shape
+        expect["fluence_dev"] = expect["fluence_dev"][:2] + (int(cfg.n_gates) * nz * ny * nx,)
+    else:
+        raise ValueError("labels_dev must be a 3-D uint8 CUDA tensor [nz, ny, nx]")
+    for name, (t, dtype, numel) in expect.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype} (accum_mode {cfg.accum_mode}), got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} must hold {numel} elements, has {t.numel()}")
     a = np.ascontiguousarray(media, dtype=np.float32).reshape(-1, 4)
     p = np.ascontiguousarray(pos, dtype=np.float32)
     d = np.ascontiguousarray(direction, dtype=np.float32)

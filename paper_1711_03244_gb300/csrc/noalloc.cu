@@ -6,7 +6,8 @@
 // cannot afford the device-wide synchronisation cudaFree may cause.  This entry point
 // runs the same walk kernel as mcx_run on the caller's device buffers (labels in,
 // fluence and tallies out) and keeps its own working memory (photon-claim counter,
-// status word, per-label tables, per-block tally partials) in the fixed array below.
+// status word, per-label tables, per-block tally and event-count partials) in the fixed
+// array below.
 //
 // The array lives in every GPU that loads this library, for the life of the process.
 // Its device address is looked up once per device, on that device's first call.  Every
@@ -58,29 +59,34 @@ __global__ void na_check_labels(const uint8_t *labels, size_t n, unsigned n_medi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
-__global__ void na_zero(float *p, size_t n)
+template <typename T>
+__global__ void na_zero(T *p, size_t n)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) p[i] = T(0);
 }
 
-// Sums the block partials (fixed order) into the caller's tally output.
-__global__ void na_finalize(const double *bt, int nblocks, double n_launched, double *out)
+// Sums the block partials (fixed order) into the caller's tally output, and the blocks'
+// counts of photons stopped by the per-photon event cap into its last word.
+__global__ void na_finalize(const double *bt, const unsigned long long *bs, int nblocks,
+                            double n_launched, double *out)
 {
-    __shared__ double st[256][MCX_NTALLY];
+    __shared__ double st[256][MCX_NTALLY + 1];
     const int tid = threadIdx.x;
-    double t[MCX_NTALLY] = {0};
-    for (int b = tid; b < nblocks; b += blockDim.x)
+    double t[MCX_NTALLY + 1] = {0};
+    for (int b = tid; b < nblocks; b += blockDim.x) {
         for (int k = 0; k < MCX_NTALLY; ++k) t[k] += bt[(size_t)b * MCX_NTALLY + k];
-    for (int k = 0; k < MCX_NTALLY; ++k) st[tid][k] = t[k];
+        t[MCX_NTALLY] += (double)bs[(size_t)b * MCX_NSTAT + MCX_STAT_CAPPED];
+    }
+    for (int k = 0; k <= MCX_NTALLY; ++k) st[tid][k] = t[k];
     __syncthreads();
     for (int h = blockDim.x / 2; h > 0; h >>= 1) {
         if (tid < h)
-            for (int k = 0; k < MCX_NTALLY; ++k) st[tid][k] += st[tid + h][k];
+            for (int k = 0; k <= MCX_NTALLY; ++k) st[tid][k] += st[tid + h][k];
         __syncthreads();
     }
     if (tid == 0) {
-        for (int k = 0; k < MCX_NTALLY; ++k) out[k] = st[0][k];
+        for (int k = 0; k <= MCX_NTALLY; ++k) out[k] = st[0][k];
         out[MCX_TALLY_LAUNCHED] = n_launched;
     }
 }
@@ -91,6 +97,7 @@ struct DeviceState {
     unsigned char *scratch = nullptr;
     LaunchShape shape{};
     int shape_block = 0;
+    int shape_accum = -1;
 };
 constexpr int kMaxDevices = 64;
 DeviceState g_dev[kMaxDevices];
@@ -102,6 +109,18 @@ mcx_status na_fail(mcx_status st, const std::string &m)
     return st;
 }
 
+// True when p is device (or managed) memory that the current device `dev` can use.
+bool device_pointer(const void *p, int dev)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();         // the failed query leaves its error behind; clear it
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) &&
+           (a.type == cudaMemoryTypeManaged || a.device == dev);
+}
+
 }  // namespace
 }  // namespace mcxg
 
@@ -111,7 +130,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
                                       uint32_t nz, float voxel_mm, uint32_t n_media,
                                       const float *props, int32_t src_kind, const float pos_mm[3],
                                       const float dir[3], float waist_mm, const mcx_run_cfg *cfg,
-                                      float *fluence_dev, double *tally_dev)
+                                      void *fluence_dev, double *tally_dev)
 {
     // ---- arguments and limits (nothing is touched on an error)
     if (!labels_dev || !props || !pos_mm || !dir || !cfg || !fluence_dev || !tally_dev)
@@ -135,11 +154,17 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     const double dn = std::sqrt((double)dir[0] * dir[0] + (double)dir[1] * dir[1] + (double)dir[2] * dir[2]);
     if ((src_kind != 0 && src_kind != 1) || !(dn > 0.0) || (src_kind == 1 && !(waist_mm > 0.f)))
         return na_fail(MCX_E_ARG, "mcx_run_noalloc: bad source");
-    if (cfg->n_gates < 1 || !(cfg->dt_ns > 0.f) || !(cfg->rr_threshold >= 0.f) ||
-        (cfg->rr_threshold > 0.f && !(cfg->rr_m > 1.f)) || cfg->precision != 0 ||
-        cfg->accum_mode != 0 || cfg->exit_log != 0 || cfg->max_detected != 0)
-        return na_fail(MCX_E_ARG, "mcx_run_noalloc: need n_gates >= 1, dt_ns > 0, valid roulette, "
-                                  "precision 0, accum_mode 0, exit_log 0, max_detected 0");
+    if (cfg->n_gates < 1 || !(cfg->dt_ns > 0.f) || !std::isfinite(cfg->dt_ns) ||
+        !std::isfinite((float)((double)cfg->dt_ns * cfg->n_gates)))
+        return na_fail(MCX_E_ARG, "mcx_run_noalloc: need n_gates >= 1 and a finite dt_ns > 0");
+    if (!(cfg->rr_threshold >= 0.f) || (cfg->rr_threshold > 0.f && !(cfg->rr_m > 1.f)))
+        return na_fail(MCX_E_ARG, "mcx_run_noalloc: need rr_threshold >= 0 and rr_m > 1");
+    if (cfg->photon_offset + cfg->n_photons < cfg->photon_offset)
+        return na_fail(MCX_E_ARG, "mcx_run_noalloc: photon id range overflows");
+    if (cfg->precision != 0 || (cfg->accum_mode != 0 && cfg->accum_mode != 2) ||
+        cfg->exit_log != 0 || cfg->max_detected != 0)
+        return na_fail(MCX_E_ARG, "mcx_run_noalloc: need precision 0, accum_mode 0 or 2, "
+                                  "exit_log 0, max_detected 0");
     const int block = cfg->block_size ? cfg->block_size : 256;
     if (block < 32 || block > 256 || block % 32)
         return na_fail(MCX_E_ARG, "mcx_run_noalloc: block_size 32..256, multiple of 32");
@@ -153,6 +178,18 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return na_fail(MCX_E_CUDA, "mcx_run_noalloc: no usable CUDA device");
+    cudaStream_t stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        (void)cudaGetLastError();
+        return na_fail(MCX_E_STATE, "mcx_run_noalloc: cannot run inside stream capture (the label "
+                                    "check waits for the stream)");
+    }
+    if (!device_pointer(labels_dev, dev) || !device_pointer(fluence_dev, dev) ||
+        !device_pointer(tally_dev, dev))
+        return na_fail(MCX_E_ARG, "mcx_run_noalloc: labels_dev, fluence_dev and tally_dev must "
+                                  "be device memory of the current device");
+    const int accum = cfg->accum_mode == 2 ? kAccF64 : kAccPlain;
     DeviceState st;
     {
         std::lock_guard<std::mutex> lock(g_mu);
@@ -166,12 +203,13 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
             d.scratch = static_cast<unsigned char *>(ptr);
             d.ready = true;
         }
-        if (d.shape_block != block) {
-            const cudaError_t e = walk_query_shape(false, Precision::F32, kAccPlain, block, kNaMaxMedia, 0,
+        if (d.shape_block != block || d.shape_accum != accum) {
+            const cudaError_t e = walk_query_shape(false, Precision::F32, accum, block, kNaMaxMedia, 0,
                                                      0, false, &d.shape);
             if (e != cudaSuccess)
                 return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: ") + cudaGetErrorString(e));
             d.shape_block = block;
+            d.shape_accum = accum;
         }
         st = d;
     }
@@ -179,7 +217,6 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     if (cfg->grid_size > 0) shape.grid = cfg->grid_size;
     if (shape.grid > kNaMaxBlocks) shape.grid = kNaMaxBlocks;
     unsigned char *scratch = st.scratch;
-    cudaStream_t stream = static_cast<cudaStream_t>(cfg->cuda_stream);
 
     // ---- tables (host set-up arithmetic), then the labels check
     TableImage img;
@@ -201,11 +238,16 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
 
     // ---- zero the caller's fluence, walk, reduce the tallies into the caller's output
     const size_t nflu = nvox * cfg->n_gates;
-    na_zero<<<(unsigned)std::min<size_t>((nflu + 255) / 256, 152u * 16u), 256, 0, stream>>>(fluence_dev, nflu);
+    const unsigned zblocks = (unsigned)std::min<size_t>((nflu + 255) / 256, 152u * 16u);
+    if (accum == kAccF64)
+        na_zero<<<zblocks, 256, 0, stream>>>(static_cast<double *>(fluence_dev), nflu);
+    else
+        na_zero<<<zblocks, 256, 0, stream>>>(static_cast<float *>(fluence_dev), nflu);
 
     WalkParams p{};
     p.labels = labels_dev;
-    p.fluence = fluence_dev;
+    if (accum == kAccF64) p.fluence64 = static_cast<double *>(fluence_dev);
+    else p.fluence = static_cast<float *>(fluence_dev);
     p.tab_a = scratch + kNaTables + (size_t)oa;
     p.tab_b = scratch + kNaTables + (size_t)ob;
     p.tab_n = scratch + kNaTables + (size_t)on;
@@ -248,10 +290,11 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.reflect = cfg->reflect;
     p.claim_chunk = kClaimChunk;
 
-    e = walk_launch(p, Precision::F32, kAccPlain, shape, stream);
+    e = walk_launch(p, Precision::F32, accum, shape, stream);
     if (e != cudaSuccess)
         return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: walk launch: ") + cudaGetErrorString(e));
-    na_finalize<<<1, 256, 0, stream>>>(p.block_tally, shape.grid, (double)cfg->n_photons, tally_dev);
+    na_finalize<<<1, 256, 0, stream>>>(p.block_tally, p.block_stats, shape.grid,
+                                        (double)cfg->n_photons, tally_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: ") + cudaGetErrorString(e));

@@ -47,7 +47,7 @@ def test_struct_layouts_match_binding(lib):
     assert cfg.n_gates == 1 and abs(cfg.rr_threshold - 1e-4) < 1e-9 and cfg.rr_m == 10.0
     assert cfg.accum_mode == 2 and cfg.precision == 0
     assert ctypes.sizeof(m.McxExit) == 40
-    assert L.mcx_abi_version() == 1
+    assert L.mcx_abi_version() == 2
 
 
 def test_status_strings(lib):
