@@ -95,7 +95,8 @@ struct Vol {
 // the window's A rows are read from shared memory once instead of three times.
 //
 // Every wait is bounded: on a timeout the role records an error and stops; the CTA still
-// waits (bounded) for its TMA loads and frees its tensor memory.
+// waits (bounded) for its TMA loads and for the MMAs it issued, then frees its tensor
+// memory.
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -243,8 +244,9 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
     // header: full[ns] at 0, empty[ns] at 64, acc full[NSLOT] at 128, acc empty[NSLOT] at
-    // 192, weights barrier at 256, TMEM address at 320
+    // 192, weights barrier at 256, MMA drain barrier at 264, TMEM address at 320
     const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 192, wbar = base + 256;
+    const uint32_t drain = base + 264;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 320 - smem_u32(smem_raw)));
     const int wtap = COUT * cin * 2, lbo_b = COUT * 16;
     const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
@@ -287,6 +289,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
             mbar_init(acce0 + 8 * a, 4 * 32);
         }
         mbar_init(wbar, 1);
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -422,6 +425,10 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
             }
             T0 += U.nz;
         }
+        // every MMA issued has completed before the CTA may free tensor memory, also when
+        // a wait above gave up (the epilogue then no longer waits for the accumulators)
+        tc_commit(drain);
+        ok &= mbar_wait(drain, 0);
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
@@ -510,9 +517,9 @@ conv3d_fwd_ws(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
     // header: full[ns] at 0, empty[ns] at 64, acc full[2 TU] at 128, acc empty[2 TU] at 256,
-    // weights full at 384, weights empty at 392, TMEM address at 448
+    // weights full at 384, weights empty at 392, MMA drain at 400, TMEM address at 448
     const uint32_t full0 = base, empty0 = base + 64, accf0 = base + 128, acce0 = base + 256;
-    const uint32_t wfull = base + 384, wempty = base + 392;
+    const uint32_t wfull = base + 384, wempty = base + 392, drain = base + 400;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 448 - smem_u32(smem_raw)));
     const int wtap = COUT * CIN * 2, lbo_b = COUT * 16;
     const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
@@ -552,6 +559,7 @@ conv3d_fwd_ws(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
         }
         mbar_init(wfull, 1);
         mbar_init(wempty, 1);
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -639,6 +647,10 @@ conv3d_fwd_ws(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 ++wpass;
             }
         }
+        // every MMA issued has completed before the CTA may free tensor memory, also when
+        // a wait above gave up (the epilogue then no longer waits for the accumulators)
+        tc_commit(drain);
+        ok &= mbar_wait(drain, 0);
     } else if (warp >= 2) {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
