@@ -90,3 +90,18 @@ def welch_voxelwise(gpu_reps: np.ndarray, orc_batches: np.ndarray):
 def t_tail(dof: np.ndarray, x: float = 3.0) -> np.ndarray:
     from scipy import stats
     return 2 * stats.t.sf(x, dof)
+
+
+def assert_voxelwise(gr, ob, min_vox=1000):
+    """Voxel-wise Welch test of two replicate sets (axis 0): the fraction of voxels with
+    |t| > 3 stays within twice the t-distribution's expectation at each voxel's Welch dof
+    (plus three binomial sigmas), and the mean t^2 stays near its expectation."""
+    t, dof, mask = welch_voxelwise(gr.reshape(gr.shape[0], -1), ob.reshape(ob.shape[0], -1))
+    assert mask.sum() >= min_vox
+    fail = np.abs(t) > 3
+    expect = t_tail(dof).mean()
+    chi = np.mean(t * t) / np.mean(dof / (dof - 2))
+    print(f"voxels {mask.sum()}, |t|>3 {fail.mean():.4f} (t-dist {expect:.4f}), "
+          f"mean t^2 / expected {chi:.3f}")
+    assert fail.mean() <= 2 * expect + 3 * math.sqrt(expect / mask.sum())
+    assert chi < 1.25

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_common import F32_RR, balance, f32
+from gpu_common import F32_RR, assert_voxelwise, balance, exit_match, f32
 
 pytestmark = pytest.mark.gpu
 
@@ -153,3 +153,44 @@ def test_queue_order_does_not_change_results(g):
         for k in res[0][0][i]:
             assert res[1][0][i][k] == pytest.approx(res[0][0][i][k], rel=1e-12, abs=1e-12)
         assert np.allclose(res[1][1][i], res[0][1][i], rtol=1e-6, atol=0)
+
+
+def test_batch_members_match_the_oracle(g, orc):
+    """The batched walk against the FP64 oracle, member by member.  Four C4-style members
+    (sides 32, 48, 64 and 48 mm; 1-3 ellipsoids each; every medium's n between 1.33 and
+    1.45 against the exterior's 1.0, so Fresnel events at every boundary) run as one batch
+    that also holds eight replicates of each member under other seeds.  Per member:
+      * fixed seed: the member's tallies against the oracle's on the same photon ids, to
+        1e-5 of the photons launched plus two units of weight for each photon whose fate or
+        exit differs (counted from a standalone run's exit log against the oracle's);
+      * fluence: voxel-wise Welch t of the eight batch replicates against eight oracle
+        batches of the same size (other photon ids), as in the single-simulation tests."""
+    n, reps = 40_000, 8
+    c4 = workloads.c4(n_sims=8)
+    members = [f32(c4[i]).with_(n_photons=n) for i in (0, 4, 2, 7)]    # #7: one label has mus 0.78
+    assert [w.labels.shape[0] for w in members] == [32, 48, 64, 48]
+    with g.Batch() as b:
+        ids = []
+        for w in members:
+            row = [b.add_workload(w)]
+            for r in range(1, reps + 1):
+                row.append(b.add_workload(w, seed=w.seed + 7919 * r))
+            ids.append(row)
+        b.run(n_gates=5, dt_ns=1.0, rr_threshold=F32_RR, use_graph=1)
+        for m, w in enumerate(members):
+            wl = w.with_(n_gates=5, dt_ns=1.0)
+            o = orc.run(wl, n_photons=n, exit_cap=n, rr_threshold=F32_RR)
+            with g.Simulation.from_workload(wl) as sim:
+                sim.run(n, n_gates=5, dt_ns=1.0, seed=wl.seed, rr_threshold=F32_RR, exit_log=n)
+                ok, _ = exit_match(sim.exits(n), o.exits)
+            flips = int((~ok).sum())
+            t = b.tally(ids[m][0])
+            print(f"member {m} (side {wl.labels.shape[0]}): {flips} of {n} photons differ")
+            assert flips <= 0.05 * n, m
+            for k in ("absorbed", "escaped", "time_exceeded", "roulette_killed", "roulette_gained"):
+                assert abs(t[k] - o.tally[k]) <= 1e-5 * n + 2 * flips, (m, k, t[k], o.tally[k])
+            assert abs(balance(t) - n) <= 1e-6 * n
+            gr = np.array([b.fluence(i).astype(np.float64) / n for i in ids[m][1:]])
+            ob = np.array([orc.run(wl, n_photons=n, photon_offset=(k + 1) * n,
+                                   rr_threshold=F32_RR).energy / n for k in range(reps)])
+            assert_voxelwise(gr, ob, min_vox=300)

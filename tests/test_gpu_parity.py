@@ -21,7 +21,8 @@ import numpy as np
 import pytest
 
 import workloads
-from gpu_common import (F32_RR, balance, exit_match, f32, gpu_run, t_tail, welch_voxelwise)
+from gpu_common import (F32_RR, assert_voxelwise as _assert_voxelwise, balance, exit_match, f32,
+                        gpu_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -117,9 +118,13 @@ def test_fixed_seed_fp32_exits(g, orc, name, bar):
     the direction at each scattering event random-walks, so the exit-point error grows
     with the number of scattering events (medians measured on GB300: about 3e-6 mm below
     500 events, 3e-4 mm beyond 5000).  In the homogeneous volume >= 99% of the first 1e4
-    photons exit within 1e-3 mm of the oracle; the heterogeneous volume adds refraction
-    at the n = 1.45 inclusion, which amplifies the difference, and the bar is 97% there.
-    Fates must agree for >= 99% in both."""
+    photons exit within 1e-3 mm of the oracle.  In the heterogeneous volume the misses sit
+    in the photons with more than 2000 scattering events (measured: 100% within 1e-3 mm
+    below 1000 events, 92% at 3000-5000, 88% beyond), where C2 falls below C1 at equal
+    event counts because free paths in the mus = 1 and mus = 5 spheres are 2-10x longer,
+    which scales the position error a given direction error makes; renormalising the
+    direction after each refraction measured no change (98.42% vs 98.44%).  The bar is 97%
+    there.  Fates must agree for >= 99% in both."""
     wl = f32(workloads.by_name(name, n_photons=10_000))
     gr = gpu_run(wl, exit_log=10_000, precision=0)
     o = orc.run(wl, exit_cap=10_000, rr_threshold=F32_RR, energy=False)
@@ -187,18 +192,6 @@ def _oracle_batches(orc, wl, n_total, k):
         o = orc.run(wl, n_photons=b, photon_offset=i * b, rr_threshold=F32_RR)
         out.append(o.energy / b)
     return np.array(out)
-
-
-def _assert_voxelwise(gr, ob, min_vox=1000):
-    t, dof, mask = welch_voxelwise(gr.reshape(gr.shape[0], -1), ob.reshape(ob.shape[0], -1))
-    assert mask.sum() >= min_vox
-    fail = np.abs(t) > 3
-    expect = t_tail(dof).mean()
-    chi = np.mean(t * t) / np.mean(dof / (dof - 2))
-    print(f"voxels {mask.sum()}, |t|>3 {fail.mean():.4f} (t-dist {expect:.4f}), "
-          f"mean t^2 / expected {chi:.3f}")
-    assert fail.mean() <= 2 * expect + 3 * math.sqrt(expect / mask.sum())
-    assert chi < 1.25
 
 
 # Replicates: 8 GPU runs (seeds 1..8) and 8 oracle batches, 1e5 photons each on both
@@ -393,6 +386,31 @@ def test_event_cap_reports_cap(g):
     assert gr["stats"]["capped"] > 250
     assert np.all(np.isin(gr["exits"]["fate"], [g.FATE_CAPPED, 1, 2, 3]))
     assert abs(balance(gr["tally"]) - 300) < 1e-5 * 300
+
+
+def test_sync_host_timeout_then_completes(g):
+    """mcx_sync polls the run's completion for at most timeout_s seconds: a 2e7-photon C2
+    run (about 0.2 s on the device) polled with a 1 ms limit returns MCX_E_TIMEOUT and
+    stays in flight; the next unbounded mcx_sync returns MCX_OK and the run's tallies close.
+    Nothing is provoked on the device: the limit is a host-side poll."""
+    import paper_1711_03244_gb300 as m
+    n = 20_000_000
+    wl = f32(workloads.c2(n_photons=n))
+    sim = m.Simulation.from_workload(wl)
+    try:
+        cfg = m.mcx_run_cfg_default(n_photons=n, n_gates=wl.n_gates, dt_ns=wl.dt_ns, seed=3,
+                                    max_detected=1_000_000)
+        sim.n_gates = wl.n_gates
+        m.mcx_run(sim.handle, cfg)
+        assert m.load().mcx_sync(sim.handle, 1e-3) == m.MCX_E_TIMEOUT
+        assert "in flight" in m.mcx_last_error(sim.handle)
+        assert m.mcx_sync(sim.handle, -1.0) == m.MCX_OK
+        t = sim.tally()
+        assert t["launched"] == n
+        assert abs(balance(t) - n) <= 1e-5 * n
+        assert sim.stats()["photons"] == n
+    finally:
+        sim.close()
 
 
 def test_reflect_zero_b1(g, orc):
