@@ -417,8 +417,8 @@ void mcx_denoiser_destroy(mcx_denoiser *d);
 /* Photon `photon`'s stream for `seed`, as the walk kernel draws it: for each of the first
    n generator outputs, out_host[5i] is the single-uniform draw (top 23 bits, also the
    first of a pair), out_host[5i+1] the second uniform of a pair draw (bits 40..18), and
-   out_host[5i+2..5i+4] the triple draw of a scattering event (bits 63..43, 42..22,
-   21..1); 5n floats. */
+   out_host[5i+2..5i+4] the triple draw of a scattering event (bits 63..43: the next hop,
+   42..22: the deflection, 21..1: the azimuth); 5n floats. */
 mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *out_host);
 
 /* Evaluates one device primitive on n input tuples (host arrays, row-major):

@@ -42,10 +42,18 @@
  * SplitMix64 sequence of the run seed (Steele, Lea & Flood 2014): photon p takes outputs
  * number 2p+1 and 2p+2.  Events that need one uniform (the first hop, Fresnel, roulette)
  * take the top 23 bits of one output; the Gaussian launch point takes two, the top 23
- * bits and bits 40..18; a scattering event takes three from one output, bits 63..43,
- * 42..22 and 21..1 (deflection, azimuth, and the next hop).  This is the per-thread
- * independent seeding of the paper's workflow, made per photon so a run is a pure
- * function of (seed, photon ids).
+ * bits and bits 40..18; a scattering event takes three from one output, bits 63..43 for
+ * the next hop, 42..22 for the deflection and 21..1 for the azimuth.  Bit 0 of a sum of
+ * the two state words is linear over GF(2) (linear complexity 128) and is never used;
+ * bit 1 is quadratic (linear complexity 8256); higher bits are of higher degree.  The hop
+ * goes through a logarithm, so its rare long hops are decided by its uniform's low-order
+ * bits: it takes the top field, and the azimuth, linear in its uniform, the bottom one.
+ * This is the per-thread independent seeding of the paper's workflow, made per photon so
+ * a run is a pure function of (seed, photon ids).
+ *
+ * Compiled with -DORC_FULL_RES_DRAWS (a test-only build) every uniform instead takes its
+ * own generator output at 53 bits, so tests can measure what the 21- and 23-bit draws do
+ * to the results.
  * ---------------------------------------------------------------------------------- */
 static uint64_t sm64_mix(uint64_t z)
 {
@@ -80,9 +88,20 @@ static uint64_t rng_next(orc_rng *g)
     return result;
 }
 
+#ifdef ORC_FULL_RES_DRAWS
+/* uniform in (0,1) from the top 53 bits k of one output: (k + 1/2) 2^-53 */
+static double rng_u53(orc_rng *g)
+{
+    return ((double)(rng_next(g) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+#endif
+
 /* uniform in (0,1): the top 23 bits k give (2k+1) * 2^-24, exact in float and double */
 static double rng_uniform(orc_rng *g)
 {
+#ifdef ORC_FULL_RES_DRAWS
+    return rng_u53(g);
+#endif
     const uint64_t k = rng_next(g) >> 41;
     return (double)(2 * k + 1) * (1.0 / 16777216.0);
 }
@@ -92,15 +111,26 @@ static double rng_uniform(orc_rng *g)
    (2k+1) 2^-24 */
 static void rng_uniform_pair(orc_rng *g, double *u1, double *u2)
 {
+#ifdef ORC_FULL_RES_DRAWS
+    *u1 = rng_u53(g);
+    *u2 = rng_u53(g);
+    return;
+#endif
     const uint64_t r = rng_next(g);
     *u1 = (double)(2 * (r >> 41) + 1) * (1.0 / 16777216.0);
     *u2 = (double)(2 * ((r >> 18) & 0x7FFFFFULL) + 1) * (1.0 / 16777216.0);
 }
 
-/* three uniforms from one output, for a scattering event (deflection, azimuth, next
-   hop): bits 63..43, 42..22 and 21..1, each as (2k+1) 2^-22 */
+/* three uniforms from one output, for a scattering event (next hop, deflection,
+   azimuth): bits 63..43, 42..22 and 21..1, each as (2k+1) 2^-22 */
 static void rng_uniform_triple(orc_rng *g, double *u1, double *u2, double *u3)
 {
+#ifdef ORC_FULL_RES_DRAWS
+    *u1 = rng_u53(g);
+    *u2 = rng_u53(g);
+    *u3 = rng_u53(g);
+    return;
+#endif
     const uint64_t r = rng_next(g);
     *u1 = (double)(2 * (r >> 43) + 1) * (1.0 / 4194304.0);
     *u2 = (double)(2 * ((r >> 22) & 0x1FFFFFULL) + 1) * (1.0 / 4194304.0);
@@ -407,8 +437,8 @@ static void run_photon(const orc_problem *P, uint64_t id, orc_ctx *C, orc_exit *
         } else {                             /* scattering event */
             C->count[ORC_C_SCATTER]++;
             ++nscat;
-            double xi_hg, xi_phi, u_hop;
-            rng_uniform_triple(&rng, &xi_hg, &xi_phi, &u_hop);
+            double u_hop, xi_hg, xi_phi;
+            rng_uniform_triple(&rng, &u_hop, &xi_hg, &xi_phi);
             const double ct = orc_hg_cos(g, xi_hg);
             const double ph = 2.0 * ORC_PI * xi_phi;
             double nd[3];

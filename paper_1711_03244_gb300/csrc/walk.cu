@@ -118,8 +118,12 @@ struct Rng {
         u1 = from_bits((unsigned)(r >> 41));
         u2 = from_bits((unsigned)(r >> 18) & 0x7fffffu);
     }
-    // Three uniforms from one output (a scattering event: deflection, azimuth, next hop):
+    // Three uniforms from one output (a scattering event: next hop, deflection, azimuth):
     // bits 63..43, 42..22 and 21..1, each (2k+1) 2^-22, exactly representable in float.
+    // Bit 0 of the generator's sum is linear over GF(2) and unused; bit 1 is quadratic.
+    // The hop's logarithm makes its rare long hops depend on the low-order bits of its
+    // uniform, so the hop takes the top field and the azimuth (linear in its uniform) the
+    // bottom one.
     __device__ __forceinline__ void triple(float &u1, float &u2, float &u3)
     {
         const uint64_t r = next();
@@ -621,8 +625,8 @@ walk_kernel(const WalkParams p)
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
                 const MedB<R> B = medB(lab);
-                float xi_hg, xi_phi, u_hop;
-                rng.triple(xi_hg, xi_phi, u_hop);
+                float u_hop, xi_hg, xi_phi;
+                rng.triple(u_hop, xi_hg, xi_phi);
                 R ct, st;
                 hg_sample(B, R(xi_hg), ct, st);
                 R sn, cs;

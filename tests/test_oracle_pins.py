@@ -130,6 +130,83 @@ def test_xorshift128plus_output_adds_the_state_words(orc):
     assert 450 <= L <= 550, L
 
 
+def _linear_complexity_np(bits):
+    """Berlekamp-Massey over GF(2) on a numpy bit vector (the same recurrence as
+    _linear_complexity, vectorised for sequences of tens of thousands of bits)."""
+    n = len(bits)
+    s = np.asarray(bits, dtype=np.uint8)
+    c = np.zeros(n + 1, np.uint8)
+    b = np.zeros(n + 1, np.uint8)
+    c[0] = b[0] = 1
+    L, m = 0, 1
+    for i in range(n):
+        d = s[i]
+        if L:
+            d ^= int(np.bitwise_and(c[1:L + 1], s[i - L:i][::-1]).sum()) & 1
+        if d == 0:
+            m += 1
+            continue
+        t = c.copy()
+        c[m:] ^= b[:n + 1 - m]
+        if 2 * L <= i:
+            L, b, m = i + 1 - L, t, 1
+        else:
+            m += 1
+    return L
+
+
+def _raw_outputs(orc, seed, photon, n):
+    """The first n 64-bit outputs of photon `photon`'s generator: the sum of the two state
+    words, then one transition."""
+    s0, s1 = orc.splitmix64_output(seed, 2 * photon + 1), orc.splitmix64_output(seed, 2 * photon + 2)
+    out = []
+    for _ in range(n):
+        out.append((s0 + s1) & (2 ** 64 - 1))
+        s0, s1 = orc.xorshift_step(s0, s1)
+    return out
+
+
+def test_low_output_bits_linear_complexity(orc):
+    """Why the draws skip bit 0 and give bit 1 to the azimuth.  Output bit k of a sum of the
+    two state words is a GF(2) polynomial of degree k + 1 in the 128 state bits (the
+    carries), so its linear complexity is at most sum_{j <= k+1} C(128, j): bit 0 is an LFSR
+    sequence of complexity 128 and bit 1 has complexity C(128, 2) + 128 = 8256, both
+    reached exactly; bit 2's bound is about 3.5e5, so over 20000 outputs it looks random
+    (complexity about half the length), as does the top bit."""
+    out = _raw_outputs(orc, 12345, 7, 20000)
+    bit = lambda k, n: [(v >> k) & 1 for v in out[:n]]
+    assert _linear_complexity_np(bit(0, 1000)) == 128
+    assert _linear_complexity_np(bit(1, 20000)) == 8256
+    assert abs(_linear_complexity_np(bit(2, 20000)) - 10000) <= 20
+    assert abs(_linear_complexity_np(bit(63, 20000)) - 10000) <= 20
+
+
+def test_triple_draw_tails(orc):
+    """The three 21-bit uniforms of a scattering event, over 4e6 events of 1000 photons:
+    the hop -ln(u) against the exponential law out to 14 mean free paths (the 21-bit grid
+    truncates it at -ln 2^-22 = 15.25, a probability of 2.4e-7 per hop, beyond this sample's
+    reach), the Henyey-Greenstein deflection (g = 0.9) against its density including the
+    backward tail, and the azimuth against the uniform law: chi^2 at p > 1e-4 each."""
+    from scipy import stats
+    u = np.concatenate([orc.uniform_triples(2024, p, 4000) for p in range(1000)])
+    hop, xi_hg, xi_phi = u[:, 0], u[:, 1], u[:, 2]
+    n = len(u)
+    # hop: bins of 0.5 mfp to 14, then [14, inf)
+    edges = np.concatenate([np.arange(0, 14.01, 0.5), [np.inf]])
+    obs, _ = np.histogram(-np.log(hop), bins=edges)
+    exp = n * (np.exp(-edges[:-1]) - np.exp(-edges[1:]))
+    assert obs[-1] > 0 and stats.chisquare(obs, exp).pvalue > 1e-4
+    g = 0.9
+    cos = np.array([orc.hg_cos(g, x) for x in xi_hg[:400_000]])
+    ce = np.linspace(-1, 1, 41)
+    cdf = lambda c: (1 - g * g) / (2 * g) * (1 / np.sqrt(1 + g * g - 2 * g * c) - 1 / (1 + g))
+    obs, _ = np.histogram(cos, bins=ce)
+    exp = len(cos) * np.diff(cdf(ce))
+    assert stats.chisquare(obs, exp).pvalue > 1e-4
+    obs, _ = np.histogram(xi_phi, bins=64, range=(0, 1))
+    assert stats.chisquare(obs).pvalue > 1e-4
+
+
 def test_uniforms_range_grid_and_moments(orc):
     u = np.concatenate([orc.uniforms(12345, p, 4096) for p in range(64)])
     assert u.min() > 0.0 and u.max() < 1.0
