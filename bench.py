@@ -51,6 +51,18 @@ OPS = {"segment": 35, "hop": 17, "scatter": 65, "face": 15, "fresnel": 25, "flus
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 SM sub-partitions x 32 lanes issue per clock
 
+# Special-function-unit operations per event of the FP32 walk: one ex2 per segment (the
+# attenuation), one lg2 per hop; per scattering event the HG reciprocal, the sine from the
+# deflection's cosine pair (square root), the azimuth's sine and cosine, the rotation's
+# reciprocal square root and the three reciprocals of the new direction; per Fresnel
+# evaluation two quotients and two square roots (incidence and refraction).
+XU_OPS = {"segment": 1, "hop": 1, "scatter": 8, "fresnel": 4}
+
+C3_WORKLOAD = "c3_layered_256x256x128"
+C3_DESC = ("256x256x128 x 0.5 mm label volume, 4 planar layers 3/7/2/rest mm (mua 0.019/0.019/"
+           "0.004/0.02, mus 7.8/9.4/0.01/6.6, g 0.89, n 1.37) in air, Gaussian beam w = 2 mm at "
+           "the top centre +z, 1e9 photons, 50 gates x 0.1 ns, FP64 accumulation map 3.4 GB")
+
 
 def algorithmic_ops(stats: dict, tally: dict) -> float:
     seg = stats["scatter"] + stats["face"] + stats["photons"]
@@ -60,31 +72,90 @@ def algorithmic_ops(stats: dict, tally: dict) -> float:
             OPS["flush"] * stats["flush"] + OPS["photon"] * stats["photons"])
 
 
+def xu_ops(stats: dict) -> float:
+    seg = stats["scatter"] + stats["face"] + stats["photons"]
+    hop = stats["scatter"] + stats["photons"]
+    return (XU_OPS["segment"] * seg + XU_OPS["hop"] * hop + XU_OPS["scatter"] * stats["scatter"] +
+            XU_OPS["fresnel"] * stats["fresnel"])
+
+
+def measure_rates(mcx, map_bytes: dict) -> dict:
+    """Measured rates (ops/s) of the resources the walk draws on (the library's
+    microbenchmarks): FMA and logic issue, the special-function unit, and FP64 atomics over
+    each workload's FP64 fluence map (and to hot words)."""
+    r = {k: mcx.mcx_probe_rate(k) for k in ("ffma", "lop3", "lg2", "ex2", "rsqrt", "sin")}
+    for name, nb in map_bytes.items():
+        r[f"red_f64_{name}"] = mcx.mcx_probe_rate("red_f64", nb)
+        r[f"red_f32_{name}"] = mcx.mcx_probe_rate("red_f32", nb // 2)
+    r["red_f64_hot"] = mcx.mcx_probe_rate("red_f64_hot")
+    return r
+
+
+def co_bounds(stats: dict, n: int, ms: float, rates: dict, map_name: str, nominal_peak: float,
+              traffic=None, hbm_gbs=None) -> dict:
+    """The walk against each resource it draws on: photons/ms that resource alone would
+    allow (rate / per-photon demand), the walk's achieved photons/ms, and the fraction.
+    The atomic bound takes the rate over an L2-resident map (the best the L2 sustains);
+    for a map larger than L2 the rate with addresses spread uniformly over all of it is
+    reported beside it as a lower bound, not used for the binding resource, since the
+    walk's deposits concentrate near the source.  With a measured DRAM traffic per launch,
+    HBM bandwidth is a bound too."""
+    ops, xu, fl = algorithmic_ops(stats, None) / n, xu_ops(stats) / n, stats["flush"] / n
+    xu_rate = min(rates[k] for k in ("lg2", "ex2", "rsqrt", "sin"))
+    at_rate = rates["red_f64_c2"]
+    achieved = n / ms
+    b = {"issue_nominal": {"per_photon": ops, "rate": nominal_peak * 1e12},
+         "issue_measured_ffma": {"per_photon": ops, "rate": rates["ffma"]},
+         "xu": {"per_photon": xu, "rate": xu_rate},
+         "l2_atomics_f64": {"per_photon": fl, "rate": at_rate}}
+    if traffic and hbm_gbs:
+        b["hbm"] = {"per_photon": traffic / n, "rate": hbm_gbs * 1e9, "unit": "bytes"}
+    for v in b.values():
+        v["bound_photons_per_ms"] = v["rate"] / v["per_photon"] / 1e3
+        v["frac"] = achieved / v["bound_photons_per_ms"]
+    binding = min((k for k in b if k != "issue_nominal"), key=lambda k: b[k]["bound_photons_per_ms"])
+    out = {"achieved_photons_per_ms": achieved, "bounds": b, "binding": binding,
+           "walk_atomics_per_s": stats["flush"] / (ms * 1e-3)}
+    if map_name != "c2":
+        r = rates[f"red_f64_{map_name}"]
+        out["atomics_spread_over_map"] = {"rate": r, "bound_photons_per_ms": r / fl / 1e3,
+                                          "frac": achieved / (r / fl / 1e3)}
+    return out
+
+
 def peaks() -> dict:
-    p = {"sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "source": "fallback"}
+    p = {"sm_max_mhz": 2070.0, "bf16_tflops": 1900.0, "hbm_gbs": 6800.0, "source": "fallback"}
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
         p["sm_max_mhz"] = float(d.get("sm_max_mhz", 2070.0))
         p["bf16_tflops"] = float(d.get("bf16_tflops", 1900.0))
+        p["hbm_gbs"] = float(d.get("hbm_gbs", 6800.0))
         p["source"] = "measured"
     return p
 
 
-def walk_traffic():
+def walk_traffic(profile: str = "walk_kernel_c2.md", photons: int = None):
     """DRAM bytes per walk launch from the committed ncu summary, if it was taken on the
-    current kernel source (matching hash); otherwise None."""
+    current kernel source (matching hash); otherwise None.  A summary taken on fewer
+    photons than the launch states its traffic per photon, which is scaled to `photons`
+    (the map's lines are refetched at a steady per-photon rate)."""
     src = os.path.join(ROOT, "paper_1711_03244_gb300", "csrc", "walk.cu")
-    prof = os.path.join(ROOT, "profiles", "walk_kernel_c2.md")
+    prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     text = open(prof).read()
     m_h = re.search(r"walk\.cu sha256\[:16\][^:\n]*:\s*([0-9a-f]{16})", text)
+    if not (m_h and m_h.group(1) == h):
+        return None
     m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
-    if m_h and m_b and m_h.group(1) == h:
+    if m_b:
         return float(m_b.group(1))
+    m_p = re.search(r"dram bytes per photon:\s*([0-9.eE+]+)", text)
+    if m_p and photons:
+        return float(m_p.group(1)) * photons
     return None
 
 
@@ -406,6 +477,30 @@ def study_denoise(args):
         d.close()
 
 
+def study_peaks(args):
+    """Measured rates of the walk's resources (issue, special-function unit, FP32/FP64
+    atomics over L2-resident and HBM-resident maps and to hot words), each the best of
+    args.steps repetitions, against the nominal issue rate."""
+    import paper_1711_03244_gb300 as mcx
+    from paper_1711_03244_gb300 import build as mcx_build
+    mcx_build.build()
+    mcx.load()
+    pk = peaks()
+    maps = {"l2_10MiB": 10 << 20, "l2_21MB_c2": 64 ** 3 * 10 * 8, "hbm_3.4GB_c3": 256 * 256 * 128 * 50 * 8}
+    best = {}
+    for _ in range(max(args.steps, 1)):
+        r = measure_rates(mcx, maps)
+        for k, v in r.items():
+            best[k] = max(best.get(k, 0.0), v)
+    nominal = SM_COUNT * LANES_PER_SM * pk["sm_max_mhz"] * 1e6
+    print(json.dumps({"study": "peaks", "rates_ops_per_s": best,
+                      "nominal_issue_thread_ops_per_s": nominal,
+                      "ffma_frac_of_nominal": best["ffma"] / nominal,
+                      "lop3_frac_of_nominal": best["lop3"] / nominal,
+                      "xu_per_sm_per_clock": {k: best[k] / SM_COUNT / (pk["sm_max_mhz"] * 1e6)
+                                              for k in ("lg2", "ex2", "rsqrt", "sin")}}), flush=True)
+
+
 def study_denoise_kernels(args):
     """The denoiser's kernels alone on synthetic inputs: one forward pass over 16 volumes of
     64^3 (every 3x3x3 convolution on tcgen05) and one training step of batch 4, each the
@@ -451,26 +546,136 @@ def study_denoise_kernels(args):
                       "forward_frac_of_peak": f_tf / pk["bf16_tflops"]}), flush=True)
 
 
+def bench_c3(args, mcx, torch, stream, rates, nominal_peak):
+    """The layered-tissue workload at its configured 1e9 photons (the largest single-GPU
+    configuration; its 3.4 GB FP64 map lives in HBM, not L2): args.c3_warmup untimed runs,
+    then args.c3_steps timed ones (CUDA events on the launching stream), the same
+    e2e measurement through the C ABI with host buffers, the roofline and co-bounds with
+    this workload's event counts, and the oracle on a bounded sample."""
+    wl = workloads.c3(n_photons=args.c3_photons)
+    n = wl.n_photons
+    sim = mcx.Simulation.from_workload(wl)
+
+    def step():
+        cfg = mcx.mcx_run_cfg_default(n_photons=n, n_gates=wl.n_gates, dt_ns=wl.dt_ns,
+                                      seed=wl.seed, cuda_stream=stream)
+        mcx.mcx_run(sim.handle, cfg)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.c3_warmup):
+        step()
+        mcx.mcx_sync(sim.handle, allow_cap=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.c3_steps)]
+    walk_ms = []
+    with ClockSampler(int(torch.cuda.current_device())) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.c3_steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            walk_ms.append(mcx.mcx_last_kernel_ms(sim.handle))
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = mcx.mcx_read_stats(sim.handle)
+    tally = mcx.mcx_read_tally(sim.handle)
+    total_ms = float(sum(step_ms))
+    walk_avg = float(np.mean(walk_ms))
+    # e2e: labels and media in from pinned host memory, run, normalised fluence and tallies
+    # back to pinned host memory, all inside the timed region
+    labels_pinned = torch.from_numpy(wl.labels).pin_memory()
+    flu_pinned = torch.empty((wl.n_gates,) + wl.labels.shape, dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for k in range(args.c3_e2e_steps + 1 if args.c3_e2e_steps > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mcx.mcx_update_labels(sim.handle, labels_pinned.numpy())
+        mcx.mcx_set_media(sim.handle, wl.media)
+        step()
+        mcx.mcx_sync(sim.handle, allow_cap=True)
+        mcx.mcx_read_fluence(sim.handle, flu_pinned.numpy(), normalized=True)
+        mcx.mcx_read_tally(sim.handle)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            e2e_times.append(dt)
+    sim.close()
+    del flu_pinned, labels_pinned
+    e2e_ms = 1e3 * float(np.mean(e2e_times)) if e2e_times else float("nan")
+    ops = algorithmic_ops(stats, tally)
+    achieved = ops / (walk_avg * 1e-3) / 1e12
+    out = {"workload": C3_WORKLOAD, "desc": C3_DESC, "value": n * args.c3_steps / total_ms,
+           "unit": UNIT, "steps": args.c3_steps, "warmup": args.c3_warmup,
+           "ms_per_step": total_ms / args.c3_steps, "photons_per_step": n,
+           "l2": "inputs larger than L2 (3.4 GB FP64 map); 256 MiB write between steps",
+           "accumulation": "FP64 L2 atomics per (gate, voxel) run (accum_mode 2)",
+           "clocks": clk.summary(),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": nominal_peak,
+                        "unit": "Tthread-op/s", "frac": achieved / nominal_peak,
+                        "traffic": walk_traffic("walk_kernel_c3.md", n),
+                        "ops_per_photon": ops / n, "kernel": "walk_kernel<float,false>",
+                        "walk_ms": walk_avg},
+           "co_bounds": co_bounds(stats, n, walk_avg, rates, "c3", nominal_peak,
+                                  walk_traffic("walk_kernel_c3.md", n), peaks()["hbm_gbs"])
+           if rates else None,
+           "e2e": {"value": n / e2e_ms if e2e_times else None, "unit": UNIT,
+                   "h2d_bytes_per_step": int(wl.labels.nbytes + wl.media.astype(np.float32).nbytes),
+                   "d2h_bytes_per_step": int(wl.n_gates * wl.labels.size * 4 + 6 * 8),
+                   "steps": args.c3_e2e_steps},
+           "events": {k: int(v) for k, v in stats.items()},
+           "energy_balance_rel": abs(tally["absorbed"] + tally["escaped"] + tally["time_exceeded"] +
+                                     tally["roulette_killed"] - tally["roulette_gained"] -
+                                     tally["launched"]) / max(tally["launched"], 1.0),
+           "gpu_launches": 5 * args.c3_steps}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        nc = args.c3_cpu_photons
+        t0 = time.perf_counter()
+        oracle.run(wl, n_photons=nc, energy=True, n_threads=cores)
+        cpu_ms = 1e3 * (time.perf_counter() - t0)
+        out["cpu_baseline"] = {"value": nc / cpu_ms, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"first {nc} photons of {C3_WORKLOAD} (FP64 oracle, "
+                                         f"{cores} OpenMP threads, {cpu_ms / 1e3:.1f} s)"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--photons", type=int, default=100_000_000)
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
+                    help="the timed workload: c2 (two-sphere volume, the metric's configuration) "
+                         "or c3 (layered tissue, 1e9 photons)")
+    ap.add_argument("--photons", type=int, default=None,
+                    help="photons per step (default 1e8 for c2, 1e9 for c3)")
     ap.add_argument("--ref-photons", type=int, default=200_000)
     ap.add_argument("--cpu-photons", type=int, default=1_500_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--c3-photons", type=int, default=1_000_000_000)
+    ap.add_argument("--c3-steps", type=int, default=2)
+    ap.add_argument("--c3-warmup", type=int, default=1,
+                    help="untimed C3 runs (the GPU is already warm from the C2 steps)")
+    ap.add_argument("--c3-e2e-steps", type=int, default=1)
+    ap.add_argument("--c3-cpu-photons", type=int, default=200_000)
+    ap.add_argument("--no-c3", action="store_true", help="skip the layered-tissue C3 leg")
+    ap.add_argument("--no-probes", action="store_true",
+                    help="skip the microbenchmarks of the issue, XU and atomic rates")
     ap.add_argument("--no-model", action="store_true",
                     help="skip the pilot runs of the linear runtime model T = a n + T0")
-    ap.add_argument("--study", default=None, choices=["paper", "batched", "denoise", "denoise-kernels"],
+    ap.add_argument("--study", default=None,
+                    choices=["paper", "batched", "denoise", "denoise-kernels", "peaks"],
                     help="paper: the paper's benchmarks B1/B2/B2a under each accumulation and "
                          "photon-distribution mode; batched: the 256-simulation batch in one "
                          "launch vs one launch per simulation; denoise: train the learned "
                          "denoiser and compare denoised and plain runs at equal error; "
                          "denoise-kernels: the denoiser's forward pass and training step "
-                         "alone (one JSON line each)")
+                         "alone; peaks: the microbenchmarked rates of the resources the walk "
+                         "draws on (one JSON line each)")
     ap.add_argument("--dn-train", type=int, default=4096, help="training volumes")
     ap.add_argument("--dn-test", type=int, default=64, help="held-out volumes")
     ap.add_argument("--dn-in", type=int, default=100_000, help="photons of an input map")
@@ -490,7 +695,13 @@ def main():
     args = ap.parse_args()
 
     world, rank, local = dist_env()
-    wl = workloads.c2(n_photons=args.photons)
+    global WORKLOAD, WORKLOAD_DESC
+    if args.workload == "c3":
+        wl = workloads.c3(n_photons=args.photons or 1_000_000_000)
+        WORKLOAD, WORKLOAD_DESC = C3_WORKLOAD, C3_DESC
+        args.no_c3 = True
+    else:
+        wl = workloads.c2(n_photons=args.photons or 100_000_000)
     if args.impl == "reference":
         run_reference(args, wl, world, rank)
         return
@@ -505,6 +716,9 @@ def main():
         return
     if args.study == "denoise-kernels":
         study_denoise_kernels(args)
+        return
+    if args.study == "peaks":
+        study_peaks(args)
         return
 
     import torch
@@ -628,11 +842,21 @@ def main():
     ops = algorithmic_ops(stats, tally)                   # per launch on this rank
     achieved = ops / (walk_avg * 1e-3) / 1e12             # T thread-op/s
     peak = SM_COUNT * LANES_PER_SM * pk["sm_max_mhz"] * 1e6 / 1e12
+    c3_main = args.workload == "c3"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tthread-op/s",
-            "frac": achieved / peak, "traffic": walk_traffic(),
+            "frac": achieved / peak,
+            "traffic": walk_traffic("walk_kernel_c3.md" if c3_main else "walk_kernel_c2.md", n),
             "peak_note": f"152 SMs x 128 lanes x {pk['sm_max_mhz']:.0f} MHz ({pk['source']} max clock)",
-            "ops_per_photon": ops / n, "kernel": "walk_kernel<float,true>",
+            "ops_per_photon": ops / n,
+            "kernel": "walk_kernel<float,false>" if c3_main else "walk_kernel<float,true>",
             "walk_ms": walk_avg}
+    rates = None
+    if not args.no_probes and rank == 0:
+        rates = measure_rates(mcx, {"c2": 64 ** 3 * 10 * 8, "c3": 256 * 256 * 128 * 50 * 8})
+        roof["peak_measured"] = rates["ffma"] / 1e12
+        roof["frac_of_measured"] = achieved / roof["peak_measured"]
+        roof["co_bounds"] = co_bounds(stats, n, walk_avg, rates, "c3" if c3_main else "c2", peak,
+                                      roof["traffic"], pk["hbm_gbs"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -677,6 +901,10 @@ def main():
             "value": n1 / one_ms, "unit": UNIT, "cores": 1,
             "sample": f"first {n1} photons of {WORKLOAD}, 1 thread, {one_ms / 1e3:.1f} s"}
     sim.close()
+    if rank == 0 and world == 1 and not args.no_c3:
+        line["c3"] = bench_c3(args, mcx, torch, stream, rates, peak)
+    if rank == 0 and rates:
+        line["measured_rates"] = rates
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -133,49 +133,62 @@ int32_t mcx_abi_version(void);
 const char *mcx_status_string(int32_t status);
 void mcx_run_cfg_default(mcx_run_cfg *cfg);
 
-/* Creates a simulation over an nx x ny x nz label volume of cubic voxels voxel_mm wide.
+/* The paper's input "domain" (workflow beside Fig. 1; the benchmark volumes beside Fig. 2
+   are such labelled voxel grids).
+   Creates a simulation over an nx x ny x nz label volume of cubic voxels voxel_mm wide.
    labels: uint8 [nz][ny][nx]; a host pointer (labels_on_device = 0) or a device pointer on
    the current device (labels_on_device = 1); copied into the handle's device memory.
    The handle binds to the CUDA device current at this call.  nx*ny*nz < 2^32. */
 mcx_status mcx_create_volume(mcx_sim **out, uint32_t nx, uint32_t ny, uint32_t nz,
                              float voxel_mm, const uint8_t *labels, int32_t labels_on_device);
 
-/* Replaces the label volume (same dimensions); invalidates previous outputs. */
+/* Replaces the label volume (same dimensions; the workflow's domain input, Fig. 1);
+   invalidates previous outputs. */
 mcx_status mcx_update_labels(mcx_sim *sim, const uint8_t *labels, int32_t labels_on_device);
 
-/* Optical properties, host array props[n_media][4] = (mua /mm, mus /mm, g, n); row m
+/* The workflow's "optical properties" input (Fig. 1); the benchmark description beside
+   Fig. 2 gives them per medium as absorption, scattering, anisotropy and index.
+   Optical properties, host array props[n_media][4] = (mua /mm, mus /mm, g, n); row m
    applies to label m; row 0 is the exterior (only its n is used).  1 <= n_media <= 256;
    every label present in the volume must have a row.  mua, mus >= 0, |g| < 1, n > 0. */
 mcx_status mcx_set_media(mcx_sim *sim, uint32_t n_media, const float *props);
 
-/* Source: kind 0 = pencil beam at pos along dir; kind 1 = Gaussian beam whose launch
+/* The workflow's source input (Fig. 1); the benchmarks beside Fig. 2 use a pencil beam.
+   Source: kind 0 = pencil beam at pos along dir; kind 1 = Gaussian beam whose launch
    points are spread over the plane normal to dir with I(r) ~ exp(-2 r^2 / waist^2).
    dir is normalised by the library.  A photon whose launch point is outside the grid or
    in a label-0 voxel is counted as escaped with fate MCX_FATE_MISSED. */
 mcx_status mcx_set_source(mcx_sim *sim, int32_t kind, const float pos_mm[3],
                           const float dir[3], float waist_mm);
 
-/* Adds a detector: a photon escaping at a point within radius_mm of center_mm is recorded
+/* Detectors produce the workflow's "detected photon data" output (Fig. 1 paragraph).
+   Adds a detector: a photon escaping at a point within radius_mm of center_mm is recorded
    (lowest detector id on overlap).  Up to 64 detectors; with detectors present the number
    of media is limited to 33 (32 tissue labels, for the partial-path record). */
 mcx_status mcx_add_detector(mcx_sim *sim, const float center_mm[3], float radius_mm,
                             int32_t *out_id);
 mcx_status mcx_clear_detectors(mcx_sim *sim);
 
-/* Enqueues one simulation on cfg->cuda_stream and returns without waiting.  Zeroes the
+/* The device side of the workflow (Fig. 1): every thread runs the photon simulation loop
+   with its own random stream; photon counts and per-thread balancing follow the
+   load-balancing discussion (Fig. 3a), as a dynamic per-warp claim by default.
+   Enqueues one simulation on cfg->cuda_stream and returns without waiting.  Zeroes the
    outputs, runs the persistent photon-walk kernel, then reduces the energy tallies.
    Output buffers are (re)allocated here when the gate count or capacities change. */
 mcx_status mcx_run(mcx_sim *sim, const mcx_run_cfg *cfg);
 
-/* Waits for the last run, polling for at most timeout_s seconds (< 0: no limit).
+/* The host's wait for the device in the workflow (Fig. 1), bounded.
+   Waits for the last run, polling for at most timeout_s seconds (< 0: no limit).
    MCX_E_TIMEOUT leaves the run in flight.  MCX_E_CAP: finished, but a capacity was hit. */
 mcx_status mcx_sync(mcx_sim *sim, double timeout_s);
 
-/* Device time of the last run's walk kernel (CUDA events on the run's stream), in ms.
+/* The simulation time the paper's speed figures are built from (photons per ms, Fig. 2).
+   Device time of the last run's walk kernel (CUDA events on the run's stream), in ms.
    Waits for the run. */
 mcx_status mcx_last_kernel_ms(mcx_sim *sim, float *ms);
 
-/* Fluence of the last run, float [n_gates][nz][ny][nx].  normalized = 0: absorbed weight
+/* The workflow's "3-D fluence maps" output and its post-processing (Fig. 1 paragraph).
+   Fluence of the last run, float [n_gates][nz][ny][nx].  normalized = 0: absorbed weight
    per voxel and gate (sum of deposited photon weight).  normalized = 1: fluence rate per
    launched photon, E / (mua h^3 N dt) in 1/(mm^2 ns), 0 where mua = 0.  dst is host memory
    (dst_on_device = 0; the call waits) or device memory on the handle's device
@@ -192,7 +205,8 @@ mcx_status mcx_read_fluence64(mcx_sim *sim, double *dst, uint64_t n_elems, int32
 /* Words (4 bytes each) per detected-photon record: 12 + (n_media - 1). */
 int32_t mcx_detected_stride(const mcx_sim *sim);
 
-/* Detected-photon records of the last run, in photon-id order, into host memory dst
+/* The workflow's "detected photon data" output (Fig. 1 paragraph).
+   Detected-photon records of the last run, in photon-id order, into host memory dst
    (cap_records * stride words).  Record layout, 32-bit words:
      [0] photon id low 32 bits, [1] high 32 bits (uint32 bit patterns)
      [2] detector id (int32)   [3] scattering events (uint32)
@@ -203,18 +217,23 @@ int32_t mcx_detected_stride(const mcx_sim *sim);
 mcx_status mcx_read_detected(mcx_sim *sim, void *dst, uint64_t cap_records,
                              uint64_t *n_written, uint64_t *n_total);
 
-/* Energy tallies (MCX_TALLY_*) of the last run, FP64, into host memory.  Waits. */
+/* Energy bookkeeping of the photon loop (absorbed, escaped, time-limited, roulette; the
+   physics the benchmarks beside Fig. 2 rely on), FP64, into host memory.  Waits. */
 mcx_status mcx_read_tally(mcx_sim *sim, double out[MCX_NTALLY]);
 
-/* Event counters (MCX_STAT_*) of the last run into host memory.  Waits. */
+/* Event counts of the photon loop (the work behind the paper's kernel profile, which
+   counts it in compute and memory instructions in its profiling observations) of the
+   last run, into host memory.  Waits. */
 mcx_status mcx_read_stats(mcx_sim *sim, uint64_t out[MCX_NSTAT]);
 
-/* Exit log of the last run (photons offset .. offset + exit_log - 1, by photon id) into
-   host memory.  Waits. */
+/* Per-photon end states for fixed-seed comparison (the paper's per-thread independent
+   seeds, Fig. 1 paragraph, made per photon id).  Exit log of the last run (photons
+   offset .. offset + exit_log - 1, by photon id) into host memory.  Waits. */
 mcx_status mcx_read_exits(mcx_sim *sim, mcx_exit *dst, uint64_t cap, uint64_t *n_written);
 
-/* Launch shape the last run used (blocks, threads per block, resident blocks per SM,
-   registers per thread). */
+/* The thread configuration the paper tunes per device (its Opt2, Fig. 2): the shape the
+   last run used (blocks, threads per block, resident blocks per SM, registers per
+   thread). */
 mcx_status mcx_launch_info(mcx_sim *sim, int32_t out[4]);
 
 const char *mcx_last_error(const mcx_sim *sim);
@@ -420,6 +439,21 @@ void mcx_denoiser_destroy(mcx_denoiser *d);
    out_host[5i+2..5i+4] the triple draw of a scattering event (bits 63..43: the next hop,
    42..22: the deflection, 21..1: the azimuth); 5n floats. */
 mcx_status mcx_debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *out_host);
+
+/* Measured rate of one device resource the walk draws on, for its roofline (the walk is
+   bound by the slowest of issue, special-function unit and L2 atomics, each rate divided by
+   the walk's per-photon demand on it; the paper reports the walk compute-bound, with 91 M
+   compute against 0.5 M memory instructions in its kernel profile).  Times the second of
+   two launches of a microbenchmark on the current device (8 blocks of 256 threads per SM):
+     kind 0: FP32 FMA issue (8 independent chains per thread), thread-ops/s
+     kind 1: three-input logic issue (LOP3, 8 chains), thread-ops/s
+     kind 2..5: special-function unit lg2 / ex2 / rsqrt / sin (approx), ops/s
+     kind 6 / 7: fire-and-forget FP32 / FP64 atomic adds to addresses hashed over a map of
+                 map_bytes (rounded down to a power of two; 4 KiB .. 64 GiB), ops/s
+     kind 8 / 9: FP32 / FP64 atomic adds, every warp's lanes to the same 32 words, ops/s
+   Allocates (and frees) its buffer; waits for the device.  MCX_E_ARG / MCX_E_OOM /
+   MCX_E_CUDA described by mcx_last_error(NULL). */
+mcx_status mcx_probe_rate(int32_t kind, uint64_t map_bytes, double *rate);
 
 /* Evaluates one device primitive on n input tuples (host arrays, row-major):
      kind 0: Henyey-Greenstein sample,  in (g, xi)                             -> out (cos, sin)

@@ -120,6 +120,7 @@ SIGNATURES = {
     "mcx_launch_info": (_i32, [_P, _P]),
     "mcx_last_error": (ctypes.c_char_p, [_P]),
     "mcx_destroy": (None, [_P]),
+    "mcx_probe_rate": (_i32, [_i32, _u64, ctypes.POINTER(_f64)]),
     "mcx_run_noalloc": (_i32, [_P, _u32, _u32, _u32, _f32, _u32, _P, _i32, _P, _P, _f32,
                                ctypes.POINTER(McxRunCfg), _P, _P]),
     "mcx_batch_cfg_default": (None, [ctypes.POINTER(McxBatchCfg)]),
@@ -382,6 +383,18 @@ def mcx_run_noalloc(labels_dev, voxel_mm: float, media, src_kind: int, pos, dire
     _check(None, load().mcx_run_noalloc(_ptr(labels_dev), nx, ny, nz, float(voxel_mm), a.shape[0],
                                         _ptr(a), int(src_kind), _ptr(p), _ptr(d), float(waist_mm),
                                         ctypes.byref(cfg), _ptr(fluence_dev), _ptr(tally_dev)))
+
+
+PROBE_KINDS = ("ffma", "lop3", "lg2", "ex2", "rsqrt", "sin", "red_f32", "red_f64",
+               "red_f32_hot", "red_f64_hot")
+
+
+def mcx_probe_rate(kind, map_bytes: int = 0) -> float:
+    """Measured rate (ops/s) of one device resource; kind is an index or a PROBE_KINDS name."""
+    k = PROBE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    r = ctypes.c_double()
+    _check(None, load().mcx_probe_rate(k, int(map_bytes), ctypes.byref(r)))
+    return r.value
 
 
 def mcx_debug_uniforms(seed: int, photon: int, n: int) -> np.ndarray:

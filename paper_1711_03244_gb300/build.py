@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcx_gb300.so")
-SOURCES = ["walk.cu", "api.cu", "noalloc.cu", "batch.cu", "denoise.cu"]
+SOURCES = ["walk.cu", "api.cu", "noalloc.cu", "batch.cu", "denoise.cu", "probe.cu"]
 HEADERS = ["mcx_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
