@@ -679,7 +679,7 @@ def main():
     ap.add_argument("--dn-train", type=int, default=4096, help="training volumes")
     ap.add_argument("--dn-test", type=int, default=64, help="held-out volumes")
     ap.add_argument("--dn-in", type=int, default=100_000, help="photons of an input map")
-    ap.add_argument("--dn-target", type=int, default=10_000_000, help="photons of a target map")
+    ap.add_argument("--dn-target", type=int, default=100_000_000, help="photons of a target map")
     ap.add_argument("--dn-ref", type=int, default=1_000_000_000, help="photons of a reference map")
     ap.add_argument("--dn-ladder-max", type=int, default=100_000_000,
                     help="largest plain run of the equal-error ladder")
