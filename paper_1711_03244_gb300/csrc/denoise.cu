@@ -74,14 +74,19 @@ struct Vol {
 // consecutive q (GEMM rows M = 128); rows that land on pad columns or past the last line
 // are computed and discarded.  In this numbering the tap (dz, dy, dx) reads row
 // q + dy * PW + dx of plane z + dz, so for a fixed dz all nine (dy, dx) taps read one
-// window of consecutive rows at offsets dy * PW + dx.  The window is one TMA box of
-// [8 channels][PW columns from x = -1][L lines][1 plane][1 volume] per 8-channel chunk:
-// the tensor map's out-of-bounds fill supplies the zero padding (x = -1, x = W, lines and
-// planes outside the volume), and the box lands in shared memory as consecutive 16-byte
-// rows in q order -- already the K-major no-swizzle operand layout (8-row core matrices
-// 128 B apart; chunks one leading-dimension offset apart), so a one-row shift of the
-// operand is a 16-byte shift of its start address.  A tile takes 3 windows (one per
-// plane); each feeds 9 taps x cin/16 tcgen05.mma instructions (K = 16, N = COUT).
+// window of consecutive rows at offsets dy * PW + dx.  In conv3d_fwd_tc the window is one
+// TMA box of [16 channels][PW columns from x = -1][L lines][1 plane][1 volume] per
+// 16-channel group: the tensor map's out-of-bounds fill supplies the zero padding
+// (x = -1, x = W, lines and planes outside the volume), and the box lands in shared
+// memory as consecutive 32-byte rows in q order, swizzled by the TMA unit in the 32-byte
+// pattern -- the K-major SWIZZLE_32B operand layout (one row holds one MMA's K = 16;
+// 8-row groups 256 B apart), so a one-row shift of the operand is a 32-byte shift of its
+// start address (the swizzle follows absolute shared addresses).  Two 16-channel groups
+// per 32-byte row halve the TMA rows of the earlier 8-channel boxes.  conv3d_fwd_ws and
+// the weight gradient stage 8-channel boxes of 16-byte rows in the no-swizzle layout
+// (8-row core matrices 128 B apart; chunks one leading-dimension offset apart).  A tile
+// takes 3 windows (one per plane); each feeds 9 taps x cin/16 tcgen05.mma instructions
+// (K = 16, N = COUT).
 //
 // Warp roles (6 warps, persistent over tiles): warp 0 lane 0 issues the TMA loads into a
 // ring of stages (mbarrier "full" with transaction bytes); warp 1 lane 0 issues the MMAs
@@ -159,13 +164,28 @@ __host__ __device__ constexpr int tc_nslot(int cin, int cout)
 __host__ __device__ constexpr int tc_lines(int w) { return (kTcRows + 2 + w + 1) / (w + 2) + 3; }
 // one 8-channel chunk of a window: L lines x PW rows of 16 B, padded to 128 B
 __host__ __device__ constexpr int tc_lbo_a(int w) { return ((tc_lines(w) * (w + 2) * 16 + 127) / 128) * 128; }
+// one 16-channel group of a window: L lines x PW rows of 32 B, swizzled in 256-byte atoms
+// (SWIZZLE_32B), padded to 1 KiB so that every group starts on a swizzle-atom boundary
+__host__ __device__ constexpr int tc_gbytes(int w) { return ((tc_lines(w) * (w + 2) * 32 + 1023) / 1024) * 1024; }
 __host__ __device__ constexpr int tc_stage_bytes(int cin, int cout, int w)
 {
-    return (cin / 8) * tc_lbo_a(w) + (tc_wall(cin, cout) ? 0 : 9 * cout * cin * 2);
+    return (cin / 16) * tc_gbytes(w) + (tc_wall(cin, cout) ? 0 : ((9 * cout * cin * 2 + 1023) / 1024) * 1024);
 }
 __host__ __device__ constexpr int tc_smem_bytes(int cin, int cout, int w, int ns)
 {
-    return 1024 + kTcFwdHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + ns * tc_stage_bytes(cin, cout, w);
+    return 1024 + kTcFwdHeader + (tc_wall(cin, cout) ? 27 * cout * cin * 2 : 0) + 1024 + ns * tc_stage_bytes(cin, cout, w);
+}
+// shared-memory descriptor of a K-major operand in the 32-byte swizzle (layout type 6):
+// rows of 32 B (K = 16 BF16, one MMA's K), 8-row groups 256 B apart (SBO); the leading
+// offset is unused at this K.  The hardware applies the swizzle on the absolute shared
+// address, so a start address shifted by any whole number of rows (the taps' row offsets)
+// needs no base offset (measured: base offset 0 reproduces the oracle, the start address's
+// bits 7..9 as base offset do not)
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr)
+{
+    const uint64_t bo = 0ull;
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(256 >> 4) << 32) | (1ull << 46) |
+           (bo << 49) | (6ull << 61);
 }
 // ring depth: each CTA has one MMA-issuing thread, so more resident CTAs issue more
 // MMAs; prefer 3-8 stages within a quarter of the SM's shared memory (4 CTAs), then 2-8
@@ -249,11 +269,11 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     const uint32_t drain = base + 264;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 320 - smem_u32(smem_raw)));
     const int wtap = COUT * cin * 2, lbo_b = COUT * 16;
-    const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_lbo_a(v.w);
-    const int a_bytes = (cin / 8) * lbo_a;
+    const int PW = v.w + 2, L = tc_lines(v.w), lbo_a = tc_gbytes(v.w);
+    const int a_bytes = (cin / 16) * lbo_a;
     const uint32_t wres = base + kTcFwdHeader;
-    const uint32_t ring = wres + (WALL ? 27 * wtap : 0);
-    const int stage_bytes = a_bytes + (WALL ? 0 : 9 * wtap);
+    const uint32_t ring = (wres + (WALL ? 27 * wtap : 0) + 1023u) & ~1023u;
+    const int stage_bytes = tc_stage_bytes(CIN, COUT, v.w);
     // merged weights: per (dy, dx) tap tt and 8-channel chunk c, the rows of dz = +1, 0, -1
     // (cout each, 16 B per row) one after another, so the tiles w - 1, w, w + 1 that a
     // window of plane w feeds are consecutive N rows; chunks LBOM bytes apart
@@ -312,7 +332,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                     tma_load_2d(dst, &tmw, 8 * c, tap * COUT, wbar);
                 }
         }
-        const uint32_t tx = a_bytes / lbo_a * (L * PW * 16) + (WALL ? 0 : 9 * wtap);
+        const uint32_t tx = (cin / 16) * (L * PW * 32) + (WALL ? 0 : 9 * wtap);
         int b = 0, use = 0;
         for (int uj = 0; uj < my_units && ok; ++uj) {
             const Unit U = unit_of(uj);
@@ -322,8 +342,8 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 if (!ok) break;
                 const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
                 mbar_expect_tx(fb, tx);
-                for (int c = 0; c < cin / 8; ++c)
-                    tma_load_5d(st + c * lbo_a, &tmx, 8 * c, -1, fl, U.z0 - 1 + j, U.b, fb);
+                for (int c = 0; c < cin / 16; ++c)
+                    tma_load_5d(st + c * lbo_a, &tmx, 16 * c, -1, fl, U.z0 - 1 + j, U.b, fb);
                 if (!WALL)                                       // one tile per unit: dz = j - 1
                     for (int tt = 0; tt < 9; ++tt)
                         for (int c = 0; c < cin / 8; ++c)
@@ -340,7 +360,6 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     } else if (tid == 32) {
         // ------------------------------------------------------------ MMA issuer
         if (WALL && my_units) ok &= mbar_wait(wbar, 0);
-        const uint64_t adesc0 = umma_desc(ring, lbo_a, 128);
         const uint64_t bdesc0 = umma_desc(WALL ? wres : ring + a_bytes, lbo_b, 128);
         int toff[9];                                            // row offset of each (dy, dx) tap
 #pragma unroll
@@ -355,7 +374,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                 tc_fence_after();
                 // descriptors differ only in the start-address field (address / 16, 14 bits;
                 // every address here is below 256 KiB): base descriptor plus an offset
-                const uint64_t abase = adesc0 + (uint64_t)((b * stage_bytes + off * 16) >> 4);
+                const uint32_t abase = ring + (uint32_t)(b * stage_bytes + off * 32);
                 if constexpr (MERGE) {
                     // tiles ilo .. ihi read this plane (tile i with dz = j - 1 - i, weight block
                     // dzi = i - j + 2); tile j starts here, tile j - 2 finishes here
@@ -380,7 +399,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                     for (int tt = 0; tt < 9; ++tt)
 #pragma unroll
                         for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                            const uint64_t ad = sw32_desc(abase + (uint32_t)(toff[tt] * 32 + kk * lbo_a));
                             const uint64_t bk = bdm + (uint64_t)((tt * 3 * wtap + 2 * kk * LBOM) >> 4);
                             // the starting tile's first product overwrites its accumulator
                             const bool fresh = starts && tt == 0 && kk == 0;
@@ -411,7 +430,7 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                     for (int tt = 0; tt < 9; ++tt)              // tt = 3 (dy + 1) + (dx + 1)
 #pragma unroll
                         for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t ad = abase + (uint64_t)(int64_t)((toff[tt] * 16 + 2 * kk * lbo_a) >> 4);
+                            const uint64_t ad = sw32_desc(abase + (uint32_t)(toff[tt] * 32 + kk * lbo_a));
                             const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
                             const uint32_t accum = (dz == -1 && tt == 0 && kk == 0) ? 0u : 1u;
                             asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -1303,6 +1322,11 @@ cudaError_t launch_tc_t(const bf16 *X, const bf16 *W, const float *bias, Vol v, 
         conv3d_fwd_ws<CIN, COUT><<<wblocks, kTcThreads, wsmem, st>>>(mx, mw, bias, v, relu, Y, err, wns);
         return cudaGetLastError();
     }
+    const cuuint32_t xbox32[5] = {16, (cuuint32_t)(v.w + 2), (cuuint32_t)tc_lines(v.w), 1, 1};
+    if (enc(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(X), xdim, xstr, xbox32, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const int ns = tc_stages(cin, COUT, v.w);
     if (ns < 2) return cudaErrorInvalidValue;                   // the volume is too wide
     const int smem = tc_smem_bytes(cin, COUT, v.w, ns);
