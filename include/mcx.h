@@ -138,7 +138,8 @@ void mcx_run_cfg_default(mcx_run_cfg *cfg);
    Creates a simulation over an nx x ny x nz label volume of cubic voxels voxel_mm wide.
    labels: uint8 [nz][ny][nx]; a host pointer (labels_on_device = 0) or a device pointer on
    the current device (labels_on_device = 1); copied into the handle's device memory.
-   The handle binds to the CUDA device current at this call.  nx*ny*nz < 2^32. */
+   The handle binds to the CUDA device current at this call.  (nx+2)(ny+2)(nz+2) < 2^32: the
+   device copy carries a one-voxel exterior border on every side. */
 mcx_status mcx_create_volume(mcx_sim **out, uint32_t nx, uint32_t ny, uint32_t nz,
                              float voxel_mm, const uint8_t *labels, int32_t labels_on_device);
 

@@ -112,9 +112,11 @@ struct TileBox {
     int lo[4], size[4];
 };
 
+// The maps and labels carry the walk's one-voxel border ([g][nz+2][ny+2][nx+2]); the
+// output is unpadded [g][nz][ny][nx].
 template <typename T>
 __global__ void resolve_kernel(int mode, const float *hi, const float *lo, const double *f64,
-                               TileBox tb, unsigned nx, unsigned ny, unsigned nvox,
+                               TileBox tb, unsigned nx, unsigned ny, unsigned nvox, unsigned pnvox,
                                unsigned n_gates, const uint8_t *labels, const float *inv_norm,
                                T *out)
 {
@@ -122,27 +124,41 @@ __global__ void resolve_kernel(int mode, const float *hi, const float *lo, const
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += stride) {
         const unsigned v = (unsigned)(i % nvox);
+        const unsigned g = (unsigned)(i / nvox);
+        const unsigned x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+        const unsigned pv = (unsigned)padded_index(x, y, z, nx, ny);
+        const size_t pi = (size_t)g * pnvox + pv;
         if (mode == 0) {
-            float f = hi[i];
-            if (inv_norm) f *= inv_norm[labels[v]];
+            float f = hi[pi];
+            if (inv_norm) f *= inv_norm[labels[pv]];
             out[i] = (T)f;
             continue;
         }
         double d;
         if (mode == 2) {
-            d = f64[i];
+            d = f64[pi];
         } else {
-            d = (double)hi[i] + (double)lo[i];
-            const unsigned g = (unsigned)(i / nvox);
-            const unsigned x = v % nx, y = (v / nx) % ny, z = v / (nx * ny);
+            d = (double)hi[pi] + (double)lo[pi];
             const unsigned tx = x - (unsigned)tb.lo[0], ty = y - (unsigned)tb.lo[1];
             const unsigned tz = z - (unsigned)tb.lo[2], tg = g - (unsigned)tb.lo[3];
             if (tx < (unsigned)tb.size[0] && ty < (unsigned)tb.size[1] &&
                 tz < (unsigned)tb.size[2] && tg < (unsigned)tb.size[3])
                 d += f64[((tg * tb.size[2] + tz) * tb.size[1] + ty) * tb.size[0] + tx];
         }
-        if (inv_norm) d *= (double)inv_norm[labels[v]];
+        if (inv_norm) d *= (double)inv_norm[labels[pv]];
         out[i] = (T)d;
+    }
+}
+
+// Copies an unpadded label volume into the interior of its bordered copy (border zeroed
+// beforehand).
+__global__ void pad_labels_kernel(const uint8_t *src, unsigned nx, unsigned ny, unsigned nz, uint8_t *dst)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned x = (unsigned)(i % nx), y = (unsigned)((i / nx) % ny), z = (unsigned)(i / ((size_t)nx * ny));
+        dst[padded_index(x, y, z, nx, ny)] = src[i];
     }
 }
 
@@ -296,19 +312,23 @@ void mcx_run_cfg_default(mcx_run_cfg *c)
     c->cuda_stream = nullptr;
 }
 
+// The device copy of the labels carries a one-voxel border of label 0 (the exterior) on
+// every side, which lets the walk step into a neighbour voxel without bounds checks.
 static mcx_status upload_labels(mcx_sim *s, const uint8_t *labels, int on_device)
 {
     const size_t n = (size_t)s->nx * s->ny * s->nz;
-    MCX_CUDA(s, s->labels.ensure(n), "allocating the label volume");
+    const size_t np = (size_t)(s->nx + 2) * (s->ny + 2) * (s->nz + 2);
+    MCX_CUDA(s, s->labels.ensure(np), "allocating the label volume");
     if (on_device) {
         cudaPointerAttributes pa;
         if (cudaPointerGetAttributes(&pa, labels) != cudaSuccess || pa.type != cudaMemoryTypeDevice)
             return fail(s, MCX_E_ARG, "labels_on_device = 1 but labels is not device memory");
-        MCX_CUDA(s, cudaMemcpy(s->labels.p, labels, n, cudaMemcpyDeviceToDevice), "copying labels");
+        MCX_CUDA(s, cudaMemset(s->labels.p, 0, np), "clearing the label volume");
+        pad_labels_kernel<<<grid_for(n), 256>>>(labels, s->nx, s->ny, s->nz, s->labels.as<uint8_t>());
         unsigned *d_max = nullptr;
         MCX_CUDA(s, cudaMalloc(&d_max, sizeof(unsigned)), "allocating");
         cudaMemset(d_max, 0, sizeof(unsigned));
-        label_max_kernel<<<grid_for(n), 256>>>(s->labels.as<uint8_t>(), n, d_max);
+        label_max_kernel<<<grid_for(np), 256>>>(s->labels.as<uint8_t>(), np, d_max);
         cudaError_t e = cudaMemcpy(&s->label_max, d_max, sizeof(unsigned), cudaMemcpyDeviceToHost);
         cudaFree(d_max);
         if (e != cudaSuccess) return cuda_fail(s, e, "label scan");
@@ -316,7 +336,12 @@ static mcx_status upload_labels(mcx_sim *s, const uint8_t *labels, int on_device
         unsigned m = 0;
         for (size_t i = 0; i < n; ++i) m = std::max<unsigned>(m, labels[i]);
         s->label_max = m;
-        MCX_CUDA(s, cudaMemcpy(s->labels.p, labels, n, cudaMemcpyHostToDevice), "copying labels");
+        std::vector<uint8_t> padded(np, 0);
+        for (uint32_t z = 0; z < s->nz; ++z)
+            for (uint32_t y = 0; y < s->ny; ++y)
+                std::memcpy(padded.data() + padded_index(0, y, z, s->nx, s->ny),
+                            labels + ((size_t)z * s->ny + y) * s->nx, s->nx);
+        MCX_CUDA(s, cudaMemcpy(s->labels.p, padded.data(), np, cudaMemcpyHostToDevice), "copying labels");
     }
     s->ran = false;
     return MCX_OK;
@@ -329,8 +354,8 @@ mcx_status mcx_create_volume(mcx_sim **out, uint32_t nx, uint32_t ny, uint32_t n
     *out = nullptr;
     if (!labels) return fail(nullptr, MCX_E_ARG, "labels is NULL");
     if (nx == 0 || ny == 0 || nz == 0) return fail(nullptr, MCX_E_ARG, "empty volume");
-    if ((uint64_t)nx * ny * nz >= (1ull << 32))
-        return fail(nullptr, MCX_E_ARG, "volume must have fewer than 2^32 voxels");
+    if ((uint64_t)(nx + 2ull) * (ny + 2ull) * (nz + 2ull) >= (1ull << 32))
+        return fail(nullptr, MCX_E_ARG, "volume must have (nx+2)(ny+2)(nz+2) < 2^32 voxels");
     if (!(voxel_mm > 0.f) || !std::isfinite(voxel_mm))
         return fail(nullptr, MCX_E_ARG, "voxel_mm must be positive and finite");
     mcx_sim *s = new (std::nothrow) mcx_sim();
@@ -510,7 +535,8 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     }
     if (cfg->grid_size > 0) shape.grid = cfg->grid_size;
 
-    const uint64_t nvox = (uint64_t)s->nx * s->ny * s->nz;
+    // maps with the walk's one-voxel border, as the label volume
+    const uint64_t nvox = (uint64_t)(s->nx + 2) * (s->ny + 2) * (s->nz + 2);
     const uint64_t nflu = nvox * cfg->n_gates;
     const int stride = kRecBase + (int)s->n_media - 1;
     MCX_CUDA(s, s->fluence.ensure(nflu * sizeof(float)), "allocating the fluence map");
@@ -571,6 +597,8 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.block_stats = s->block_stats.as<unsigned long long>();
     p.nx = (int)s->nx; p.ny = (int)s->ny; p.nz = (int)s->nz;
     p.nvox = (unsigned)nvox;
+    p.sy = s->nx + 2;
+    p.sz = (s->nx + 2) * (s->ny + 2);
     p.n_media = (int)s->n_media;
     p.n_det = n_det;
     p.rec_stride = stride;
@@ -707,18 +735,11 @@ static mcx_status read_fluence_t(mcx_sim *s, T *dst, uint64_t n_elems, int32_t n
     if (!s->ran) return fail(s, MCX_E_STATE, "no run");
     DeviceGuard g(s->device);
     const uint64_t nvox = (uint64_t)s->nx * s->ny * s->nz;
+    const uint64_t pnvox = (uint64_t)(s->nx + 2) * (s->ny + 2) * (s->nz + 2);
     const uint64_t n = nvox * s->cfg.n_gates;
     if (n_elems != n) return fail(s, MCX_E_ARG, "n_elems must be n_gates*nx*ny*nz = " + std::to_string(n));
     cudaStream_t st = s->stream;
     const int mode = s->cfg.accum_mode;
-    // the raw FP32 map can be copied as it is
-    if (mode == kAccPlain && !normalized && sizeof(T) == sizeof(float)) {
-        MCX_CUDA(s, cudaMemcpyAsync(dst, s->fluence.p, n * sizeof(float),
-                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st),
-                 "copying the fluence");
-        if (!dst_on_device) MCX_CUDA(s, cudaStreamSynchronize(st), "waiting for the copy");
-        return MCX_OK;
-    }
     const float *inv_dev = nullptr;
     if (normalized) {
         // inv_norm[label] = 1 / (mua h^3 N dt), 0 where mua = 0 or N = 0
@@ -748,7 +769,7 @@ static mcx_status read_fluence_t(mcx_sim *s, T *dst, uint64_t n_elems, int32_t n
     resolve_kernel<T><<<grid_for(n), 256, 0, st>>>(mode, s->fluence.as<float>(),
                                                    s->fluence_lo.as<float>(),
                                                    s->fluence64.as<double>(), tb, s->nx, s->ny,
-                                                   (unsigned)nvox, s->cfg.n_gates,
+                                                   (unsigned)nvox, (unsigned)pnvox, s->cfg.n_gates,
                                                    s->labels.as<uint8_t>(), inv_dev, out);
     MCX_CUDA(s, cudaGetLastError(), "launching the fluence read-out");
     if (dst_on_device) return MCX_OK;

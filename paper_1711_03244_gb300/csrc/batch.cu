@@ -66,15 +66,20 @@ __global__ void batch_stats(const unsigned long long *bs, int nblocks, unsigned 
         for (int k = 0; k < MCX_NSTAT; ++k) out[k] = ss[0][k];
 }
 
-// one simulation's map as float, optionally normalised per launched photon
+// one simulation's map as float [g][nz][ny][nx], optionally normalised per launched
+// photon; the map and the labels carry the walk's one-voxel border
 __global__ void batch_resolve(const float *f32, const double *f64, const uint8_t *labels,
-                              const float *inv_norm, unsigned nvox, size_t n, float *out)
+                              const float *inv_norm, unsigned nx, unsigned ny, unsigned nvox,
+                              unsigned pnvox, size_t n, float *out)
 {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        double v = f64 ? f64[i] : (double)f32[i];
-        if (inv_norm) v *= (double)inv_norm[labels[i % nvox]];
-        out[i] = (float)v;
+        const unsigned v = (unsigned)(i % nvox), g = (unsigned)(i / nvox);
+        const unsigned pv = (unsigned)padded_index(v % nx, (v / nx) % ny, v / (nx * ny), nx, ny);
+        const size_t pi = (size_t)g * pnvox + pv;
+        double x = f64 ? f64[pi] : (double)f32[pi];
+        if (inv_norm) x *= (double)inv_norm[labels[pv]];
+        out[i] = (float)x;
     }
 }
 
@@ -204,8 +209,8 @@ mcx_status mcx_batch_add(mcx_batch *b, uint32_t nx, uint32_t ny, uint32_t nz, fl
 {
     if (!b) return bfail(nullptr, MCX_E_ARG, "batch is NULL");
     if (!labels || !props || !pos || !dir) return bfail(b, MCX_E_ARG, "NULL argument");
-    if (nx == 0 || ny == 0 || nz == 0 || (uint64_t)nx * ny * nz >= (1ull << 32))
-        return bfail(b, MCX_E_ARG, "need 0 < nx*ny*nz < 2^32");
+    if (nx == 0 || ny == 0 || nz == 0 || (uint64_t)(nx + 2ull) * (ny + 2ull) * (nz + 2ull) >= (1ull << 32))
+        return bfail(b, MCX_E_ARG, "need nx, ny, nz > 0 and (nx+2)(ny+2)(nz+2) < 2^32");
     if (!(voxel_mm > 0.f) || n_media < 1 || n_media > (uint32_t)kMaxMedia)
         return bfail(b, MCX_E_ARG, "bad voxel size or media count");
     for (uint32_t m = 0; m < n_media; ++m) {
@@ -245,8 +250,14 @@ mcx_status mcx_batch_add(mcx_batch *b, uint32_t nx, uint32_t ny, uint32_t nz, fl
     s->frac.assign(n_media, 0.0);
     for (const uint8_t l : host) s->frac[l] += 1.0;
     for (double &f : s->frac) f /= (double)nv;
-    if (s->labels.ensure(nv) != cudaSuccess ||
-        cudaMemcpy(s->labels.p, host.data(), nv, cudaMemcpyHostToDevice) != cudaSuccess) {
+    // the device copy carries a one-voxel exterior border (label 0) on every side
+    const size_t np = (size_t)(nx + 2) * (ny + 2) * (nz + 2);
+    std::vector<uint8_t> padded(np, 0);
+    for (uint32_t z = 0; z < nz; ++z)
+        for (uint32_t y = 0; y < ny; ++y)
+            std::memcpy(padded.data() + padded_index(0, y, z, nx, ny), host.data() + ((size_t)z * ny + y) * nx, nx);
+    if (s->labels.ensure(np) != cudaSuccess ||
+        cudaMemcpy(s->labels.p, padded.data(), np, cudaMemcpyHostToDevice) != cudaSuccess) {
         delete s;
         return bfail(b, MCX_E_OOM, "allocating the label volume");
     }
@@ -272,7 +283,7 @@ static mcx_status layout(mcx_batch *b, const mcx_batch_cfg *cfg, double fraction
     int rows = 0;
     for (size_t i = 0; i < n; ++i) {
         b->flu_off[i] = vox_total * cfg->n_gates;
-        vox_total += (uint64_t)b->sims[i]->nx * b->sims[i]->ny * b->sims[i]->nz;
+        vox_total += (uint64_t)(b->sims[i]->nx + 2) * (b->sims[i]->ny + 2) * (b->sims[i]->nz + 2);
         rows += (int)b->sims[i]->n_media;
     }
     BCUDA(b, b->fluence.ensure(vox_total * cfg->n_gates * elt), "allocating the batch fluence maps");
@@ -314,7 +325,9 @@ static mcx_status layout(mcx_batch *b, const mcx_batch_cfg *cfg, double fraction
         if (s->n_photons == 0) D.n_photons = 0;
         D.seed = s->seed;
         D.nx = (int)s->nx; D.ny = (int)s->ny; D.nz = (int)s->nz;
-        D.nvox = s->nx * s->ny * s->nz;
+        D.nvox = (s->nx + 2) * (s->ny + 2) * (s->nz + 2);
+        D.sy = s->nx + 2;
+        D.sz = (s->nx + 2) * (s->ny + 2);
         D.tab0 = row;
         D.src_kind = s->kind;
         double e1[3], e2[3];
@@ -523,7 +536,7 @@ mcx_status mcx_batch_read_fluence(mcx_batch *b, int32_t id, float *dst, uint64_t
     batch_resolve<<<grid_of(n), 256, 0, b->stream>>>(
         f64 ? nullptr : b->fluence.as<float>() + b->flu_off[id],
         f64 ? b->fluence.as<double>() + b->flu_off[id] : nullptr, s->labels.as<uint8_t>(), inv,
-        (unsigned)nvox, n, out);
+        s->nx, s->ny, (unsigned)nvox, (s->nx + 2) * (s->ny + 2) * (s->nz + 2), n, out);
     BCUDA(b, cudaGetLastError(), "launching the read-out");
     if (!dst_on_device) {
         BCUDA(b, cudaMemcpyAsync(dst, out, n * sizeof(float), cudaMemcpyDeviceToHost, b->stream), "copying");

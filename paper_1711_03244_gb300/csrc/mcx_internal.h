@@ -46,14 +46,18 @@ struct BatchSim {
     unsigned long long n_photons;
     unsigned long long seed;
     int nx, ny, nz;
-    unsigned nvox;
+    unsigned nvox;                    // voxels of the padded volume (nx+2)(ny+2)(nz+2)
+    unsigned sy, sz;                  // padded strides: nx + 2, (nx + 2)(ny + 2)
     int tab0;                         // first row of this simulation in the batch tables
     int src_kind;
     float src_pos[3], src_dir[3], src_e1[3], src_e2[3], waist;
 };
 
 struct WalkParams {
-    const uint8_t *labels;            // [nz][ny][nx]
+    // Volumes (labels and the accumulation maps) carry a one-voxel exterior border on every
+    // side ([nz+2][ny+2][nx+2]) except in the allocation-free run, whose caller-owned
+    // buffers are unpadded; nvox, sy and sz describe the layout actually used.
+    const uint8_t *labels;            // [nz][ny][nx] (+ border)
     float *fluence;                   // [n_gates][nvox] absorbed weight (accum 1: the hi part)
     float *fluence_lo;                // accum 1: [n_gates][nvox] the lo part
     double *fluence64;                // accum 2: [n_gates][nvox]; accum 1: the tile's FP64 map
@@ -72,8 +76,9 @@ struct WalkParams {
     unsigned long long *block_stats;  // [grid][MCX_NSTAT]
     unsigned *status;
 
-    int nx, ny, nz;
-    unsigned nvox;
+    int nx, ny, nz;                   // the volume's voxels (without border)
+    unsigned nvox;                    // voxels per gate of the maps (with border, if any)
+    unsigned sy, sz;                  // linear strides of y and z in the labels and maps
     int src_kind;
     int n_media;
     int n_det;
@@ -121,6 +126,11 @@ cudaError_t walk_launch(const WalkParams &p, Precision prec, int accum, const La
                         cudaStream_t stream);
 // batch walk: FP32 photon state, accumulation 0 or 2, no detectors or exit log
 cudaError_t walk_batch_query_shape(int accum, int block, LaunchShape *shape);
+// unpadded caller-owned volume and map (allocation-free run): FP32 walk, no detectors,
+// accumulation 0 or 2
+cudaError_t walk_query_shape_unpadded(int accum, int block, LaunchShape *shape);
+cudaError_t walk_launch_unpadded(const WalkParams &p, int accum, const LaunchShape &shape,
+                                 cudaStream_t stream);
 cudaError_t walk_batch_launch(const WalkParams &p, int accum, const LaunchShape &shape,
                               cudaStream_t stream);
 // Gaussian launch plane of a beam along unit vector d: e1 = normalise(d x z) (x when the
@@ -144,5 +154,12 @@ void set_global_error(const std::string &msg);
 
 cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out);
 cudaError_t debug_primitive(int kind, uint64_t n, const float *dev_in, float *dev_out);
+
+// Padded volume layout: index of voxel (x, y, z) of an nx x ny volume in its bordered copy.
+__host__ __device__ inline unsigned long long padded_index(unsigned x, unsigned y, unsigned z,
+                                                        unsigned nx, unsigned ny)
+{
+    return ((unsigned long long)(z + 1) * (ny + 2) + (y + 1)) * (nx + 2) + (x + 1);
+}
 
 }  // namespace mcxg

@@ -204,8 +204,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
             d.ready = true;
         }
         if (d.shape_block != block || d.shape_accum != accum) {
-            const cudaError_t e = walk_query_shape(false, Precision::F32, accum, block, kNaMaxMedia, 0,
-                                                     0, false, &d.shape);
+            const cudaError_t e = walk_query_shape_unpadded(accum, block, &d.shape);
             if (e != cudaSuccess)
                 return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: ") + cudaGetErrorString(e));
             d.shape_block = block;
@@ -259,7 +258,9 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.block_tally = reinterpret_cast<double *>(scratch + kNaTally);
     p.block_stats = reinterpret_cast<unsigned long long *>(scratch + kNaStats);
     p.nx = (int)nx; p.ny = (int)ny; p.nz = (int)nz;
-    p.nvox = (unsigned)nvox;
+    p.nvox = (unsigned)nvox;                       // the caller's unpadded layout
+    p.sy = nx;
+    p.sz = nx * ny;
     p.n_media = (int)n_media;
     p.n_det = 0;
     p.rec_stride = kRecBase + (int)n_media - 1;
@@ -290,7 +291,7 @@ extern "C" mcx_status mcx_run_noalloc(const uint8_t *labels_dev, uint32_t nx, ui
     p.reflect = cfg->reflect;
     p.claim_chunk = kClaimChunk;
 
-    e = walk_launch(p, Precision::F32, accum, shape, stream);
+    e = walk_launch_unpadded(p, accum, shape, stream);
     if (e != cudaSuccess)
         return na_fail(MCX_E_CUDA, std::string("mcx_run_noalloc: walk launch: ") + cudaGetErrorString(e));
     na_finalize<<<1, 256, 0, stream>>>(p.block_tally, p.block_stats, shape.grid,

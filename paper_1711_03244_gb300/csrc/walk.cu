@@ -263,7 +263,12 @@ template <> __device__ __forceinline__ const RunConsts<float> &consts<float>(con
 template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(const WalkParams &p)
 { return p.cd; }
 
-template <typename R, bool DET, int ACC, bool STATIC, bool BATCH>
+// PAD: the label volume and the accumulation maps carry a one-voxel exterior border, so
+// the neighbour of any tissue voxel is inside the arrays: the face step reads its label
+// without per-axis bounds checks, and the per-axis voxel indices need not be carried
+// (they are recovered from the linear index when a photon ends).  Caller-owned unpadded
+// buffers (the allocation-free run) take PAD = false.
+template <typename R, bool DET, int ACC, bool STATIC, bool BATCH, bool PAD>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BATCH ? 3 : 4) : 1)
 walk_kernel(const WalkParams p)
 {
@@ -308,8 +313,8 @@ walk_kernel(const WalkParams p)
     double *G_flu64 = p.fluence64;
     int G_nx = p.nx, G_ny = p.ny, G_nz = p.nz;
     unsigned G_nvox = p.nvox;
+    unsigned G_sy = p.sy, G_sz = p.sz;     // linear strides of y and z (padded when PAD)
     int tab0 = 0, sim = 0;
-    unsigned nxy = (unsigned)p.nx * (unsigned)p.ny;
     // per-label tables: shared memory, or (batch) the batch tables through L1
     auto medA = [&](int l) -> MedA<R> {
         if constexpr (BATCH) {
@@ -440,7 +445,7 @@ walk_kernel(const WalkParams p)
                             rng.seed(S.seed, pid);
                             G_labels = S.labels; G_flu = S.fluence; G_flu64 = S.fluence64;
                             G_nx = S.nx; G_ny = S.ny; G_nz = S.nz; G_nvox = S.nvox;
-                            nxy = (unsigned)S.nx * (unsigned)S.ny;
+                            G_sy = S.sy; G_sz = S.sz;
                             tab0 = S.tab0;
                             px = S.src_pos[0]; py = S.src_pos[1]; pz = S.src_pos[2];
                             ux = S.src_dir[0]; uy = S.src_dir[1]; uz = S.src_dir[2];
@@ -481,7 +486,8 @@ walk_kernel(const WalkParams p)
                         const bool inside = (unsigned)ix < (unsigned)G_nx &&
                                             (unsigned)iy < (unsigned)G_ny &&
                                             (unsigned)iz < (unsigned)G_nz;
-                        vlin = inside ? ((unsigned)iz * nxy + (unsigned)iy * (unsigned)G_nx + (unsigned)ix) : 0u;
+                        vlin = inside ? ((unsigned)iz * G_sz + (unsigned)iy * G_sy + (unsigned)ix +
+                                         (PAD ? G_sz + G_sy + 1u : 0u)) : 0u;
                         lab = inside ? (int)__ldg(G_labels + vlin) : 0;
                         alive = lab != 0;
                         if (alive) {
@@ -559,19 +565,32 @@ walk_kernel(const WalkParams p)
                 const bool p0 = ax == 0, p1 = ax == 1;
                 const R inv_a = p0 ? iux : (p1 ? iuy : iuz);
                 const bool up = inv_a > R(0);              // u_ax >= 0 (inv_dir of 0 is +huge)
-                const int ia = (p0 ? ix : (p1 ? iy : iz)) + (up ? 1 : -1);
-                const int dim = p0 ? G_nx : (p1 ? G_ny : G_nz);
-                const unsigned stride = p0 ? 1u : (p1 ? (unsigned)G_nx : nxy);
+                const unsigned stride = p0 ? 1u : (p1 ? G_sy : G_sz);
                 const unsigned nlin = up ? vlin + stride : vlin - stride;
-                const bool inside = (unsigned)ia < (unsigned)dim;
-                const int b = inside ? (int)__ldg(G_labels + nlin) : 0;
+                // per-axis index of the next voxel: tracked unless the border makes it
+                // unnecessary (the compensated mode's block tile still needs it)
+                constexpr bool AXES = !PAD || ACC == kAccCompensated;
+                int ia = 0;
+                if constexpr (AXES) ia = (p0 ? ix : (p1 ? iy : iz)) + (up ? 1 : -1);
+                int b;
+                if constexpr (PAD) {
+                    b = (int)__ldg(G_labels + nlin);
+                } else {
+                    const int dim = p0 ? G_nx : (p1 ? G_ny : G_nz);
+                    b = (unsigned)ia < (unsigned)dim ? (int)__ldg(G_labels + nlin) : 0;
+                }
                 if (b == lab) {
                     // same medium: straight into the next voxel, entering on the near face
                     flush();                              // the deposit run ends with the voxel
                     const R qn = up ? R(0) : R(1);
-                    ix = p0 ? ia : ix; qx = p0 ? qn : qx;
-                    iy = p1 ? ia : iy; qy = p1 ? qn : qy;
-                    iz = (!p0 && !p1) ? ia : iz; qz = (!p0 && !p1) ? qn : qz;
+                    qx = p0 ? qn : qx;
+                    qy = p1 ? qn : qy;
+                    qz = (!p0 && !p1) ? qn : qz;
+                    if constexpr (AXES) {
+                        ix = p0 ? ia : ix;
+                        iy = p1 ? ia : iy;
+                        iz = (!p0 && !p1) ? ia : iz;
+                    }
                     vlin = nlin;
                     if (s <= R(0)) new_hop();            // hop used up by rounding at the face
                 } else {
@@ -593,7 +612,7 @@ walk_kernel(const WalkParams p)
                             ++c_fres;
                             const R ci = fabs(ua);
                             const R eta = M<R>::div(na, nb);
-                            const R st2 = eta * eta * (R(1) - ci * ci);
+                            const R st2 = eta * eta * fma(-ci, ci, R(1));   // one rounding
                             bool refl = true;                 // total internal reflection
                             if (st2 < R(1)) refl = R(rng.uniform()) < fresnel(na, nb, ci, st2);
                             if (refl) {
@@ -617,9 +636,11 @@ walk_kernel(const WalkParams p)
                     }
                     if (enter) {
                         flush();
-                        ix = p0 ? ia : ix;
-                        iy = p1 ? ia : iy;
-                        iz = !p0 && !p1 ? ia : iz;
+                        if constexpr (AXES) {
+                            ix = p0 ? ia : ix;
+                            iy = p1 ? ia : iy;
+                            iz = !p0 && !p1 ? ia : iz;
+                        }
                         qx = p0 ? R(1) - qb : qx;
                         qy = p1 ? R(1) - qb : qy;
                         qz = !p0 && !p1 ? R(1) - qb : qz;
@@ -686,6 +707,13 @@ walk_kernel(const WalkParams p)
         if (fate == MCX_FATE_CAPPED) {
             atomicAdd(&s_stats[MCX_STAT_CAPPED], 1ull);
             atomicOr(p.status, kStatusCapped);
+        }
+        if constexpr (PAD && ACC != kAccCompensated) {
+            // the voxel's indices from its linear index in the padded volume
+            const unsigned r = vlin % G_sz;
+            iz = (int)(vlin / G_sz) - 1;
+            iy = (int)(r / G_sy) - 1;
+            ix = (int)(r % G_sy) - 1;
         }
         const R hh = R(p.h);
         const R ex = (R(ix) + qx) * hh, ey = (R(iy) + qy) * hh, ez = (R(iz) + qz) * hh;
@@ -779,7 +807,7 @@ __global__ void primitive_kernel(int kind, uint64_t n, const float *in, float *o
     } else {
         const float n1 = in[3 * i], n2 = in[3 * i + 1], ci = in[3 * i + 2];
         const float eta = M<float>::div(n1, n2);
-        const float st2 = eta * eta * (1.f - ci * ci);
+        const float st2 = eta * eta * fmaf(-ci, ci, 1.f);
         out[i] = st2 < 1.f ? fresnel(n1, n2, ci, st2) : 1.f;
     }
 }
@@ -831,22 +859,22 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
     *ot = (const void *)t;
 }
 
-template <typename R, bool DET, int ACC, bool ST, bool BATCH = false>
+template <typename R, bool DET, int ACC, bool ST, bool BATCH = false, bool PAD = true>
 cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape *shape)
 {
     const size_t smem = SmemLayout<R>(n_media, DET ? n_det : 0, tile_e).total;
-    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC, ST, BATCH>,
+    cudaError_t e = cudaFuncSetAttribute(walk_kernel<R, DET, ACC, ST, BATCH, PAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC, ST, BATCH>,
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<R, DET, ACC, ST, BATCH, PAD>,
                                                            block, smem)) != cudaSuccess)
         return e;
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC, ST, BATCH>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, walk_kernel<R, DET, ACC, ST, BATCH, PAD>)) != cudaSuccess) return e;
     shape->block = block;
     shape->blocks_per_sm = per_sm;
     shape->grid = sms * (per_sm > 0 ? per_sm : 1);
@@ -854,13 +882,13 @@ cudaError_t shape_for(int block, int n_media, int n_det, int tile_e, LaunchShape
     return cudaSuccess;
 }
 
-template <typename R, bool DET, int ACC, bool ST, bool BATCH = false>
+template <typename R, bool DET, int ACC, bool ST, bool BATCH = false, bool PAD = true>
 cudaError_t launch(const WalkParams &p, const LaunchShape &s, cudaStream_t st)
 {
     const int tile_e = ACC == kAccCompensated
         ? p.tile_size[0] * p.tile_size[1] * p.tile_size[2] * p.tile_size[3] : 0;
     const size_t smem = SmemLayout<R>(BATCH ? 0 : p.n_media, DET ? p.n_det : 0, tile_e).total;
-    walk_kernel<R, DET, ACC, ST, BATCH><<<s.grid, s.block, smem, st>>>(p);
+    walk_kernel<R, DET, ACC, ST, BATCH, PAD><<<s.grid, s.block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
@@ -948,6 +976,18 @@ cudaError_t walk_batch_launch(const WalkParams &p, int accum, const LaunchShape 
 {
     if (accum == kAccF64) return launch<float, false, kAccF64, false, true>(p, s, st);
     return launch<float, false, kAccPlain, false, true>(p, s, st);
+}
+
+cudaError_t walk_query_shape_unpadded(int accum, int block, LaunchShape *shape)
+{
+    if (accum == kAccF64) return shape_for<float, false, kAccF64, false, false, false>(block, 32, 0, 0, shape);
+    return shape_for<float, false, kAccPlain, false, false, false>(block, 32, 0, 0, shape);
+}
+
+cudaError_t walk_launch_unpadded(const WalkParams &p, int accum, const LaunchShape &s, cudaStream_t st)
+{
+    if (accum == kAccF64) return launch<float, false, kAccF64, false, false, false>(p, s, st);
+    return launch<float, false, kAccPlain, false, false, false>(p, s, st);
 }
 
 cudaError_t debug_uniforms(uint64_t seed, uint64_t photon, uint64_t n, float *dev_out)

@@ -139,6 +139,11 @@ def test_fixed_seed_fp32_exits(g, orc, name, bar):
 
 
 def test_launch_shape_does_not_change_trajectories(g):
+    """Grid and block shape do not change a single bit of any photon's history (the same
+    compiled kernel, each photon's stream fixed by its id), and neither does the static
+    per-thread split, a separately compiled kernel: the walk writes the arithmetic whose
+    fusion the code generator could otherwise choose per kernel (the refraction's sin^2)
+    as explicit FMAs, so every instantiation rounds it alike."""
     wl = _c1(3000)
     a = gpu_run(wl, exit_log=3000)
     b = gpu_run(wl, exit_log=3000, block_size=64, grid_size=7)
@@ -146,6 +151,7 @@ def test_launch_shape_does_not_change_trajectories(g):
     d = gpu_run(wl, exit_log=3000, claim_mode=1)             # static per-thread split
     assert np.array_equal(a["exits"], b["exits"]) and np.array_equal(a["exits"], c["exits"])
     assert np.array_equal(a["exits"], d["exits"])
+    assert a["tally"]["absorbed"] == d["tally"]["absorbed"]
     assert d["stats"]["photons"] == 3000
 
 
