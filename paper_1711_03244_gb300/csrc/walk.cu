@@ -268,8 +268,10 @@ template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(c
 // without per-axis bounds checks, and the per-axis voxel indices need not be carried
 // (they are recovered from the linear index when a photon ends).  Caller-owned unpadded
 // buffers (the allocation-free run) take PAD = false.
+// FP32: 4 resident blocks of 256 threads per SM (64 registers; the batch instantiation fits
+// them too since the bordered volume freed its per-axis indices)
 template <typename R, bool DET, int ACC, bool STATIC, bool BATCH, bool PAD>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (BATCH ? 3 : 4) : 1)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
 walk_kernel(const WalkParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
