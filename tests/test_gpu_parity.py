@@ -494,3 +494,23 @@ def test_full_size_c2_sampled(g, orc):
     assert ok.mean() >= 0.97
     assert (gr["exits"]["fate"] == o.exits["fate"]).mean() >= 0.99
     assert gr["det_total"] > 0 and len(gr["det"]["id"]) == gr["det_total"]
+
+
+def test_full_size_c3_sampled(g, orc):
+    """The largest configuration at its size: the layered 256x256x128 volume with a
+    Gaussian beam, 1e9 photons in the default launch shape, 50 gates and a 3.5 GB FP64
+    map.  Sampled outputs the oracle can compute one by one (the first 1e4 photons' fates
+    and exit points, by id) and properties that hold at any size: the photon count, the
+    energy balance, and the map holding exactly what the absorbed tally says."""
+    wl = f32(workloads.c3())
+    gr = gpu_run(wl, exit_log=10_000)
+    t = gr["tally"]
+    assert t["launched"] == 1e9 and gr["stats"]["photons"] == 1_000_000_000
+    assert abs(balance(t) - 1e9) / 1e9 < 1e-5
+    assert abs(gr["energy"].sum(dtype=np.float64) - t["absorbed"]) / t["absorbed"] < 1e-6
+    o = orc.run(wl, n_photons=10_000, exit_cap=10_000, rr_threshold=F32_RR, energy=False)
+    ok, d = exit_match(gr["exits"], o.exits)
+    fate = (gr["exits"]["fate"] == o.exits["fate"]).mean()
+    print(f"c3 full size, first 1e4 photons: exits within 1e-3 mm {ok.mean():.4f}, fates {fate:.4f}")
+    assert ok.mean() >= 0.97
+    assert fate >= 0.99
