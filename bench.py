@@ -270,7 +270,7 @@ def study_paper(args):
     rows = [("B1", 2, 0), ("B1", 0, 0), ("B1", 1, 0), ("B1", 2, 1),
             ("B2a", 2, 0), ("B2a", 0, 0), ("B2a", 1, 0), ("B2a", 2, 1)]
     for name, accum, claim in rows:
-        wl = workloads.paper_b("B1" if name == "B1" else "B2", n_photons=args.photons)
+        wl = workloads.paper_b("B1" if name == "B1" else "B2", n_photons=args.photons or 100_000_000)
         with mcx.Simulation.from_workload(wl) as sim:
             def step():
                 cfg = mcx.mcx_run_cfg_default(n_photons=wl.n_photons, n_gates=wl.n_gates,
