@@ -92,8 +92,9 @@ typedef struct mcx_run_cfg {
                                          rounding error of each hi addition recovered exactly
                                          (TwoSum on the atomic's old value) into lo; each block
                                          flushes its tile once, in FP64, into the tile's FP64 map;
-                                         runs outside the tile go to a global (hi, lo) pair the
-                                         same way; the result is hi + lo + tile;
+                                         runs outside the tile go to a global (hi, lo) pair (the
+                                         two words adjacent) the same way; the result is
+                                         hi + lo + tile;
                                       2: FP64 global atomics (the default: exact to FP64
                                          rounding, and measured as fast as mode 0 on GB300,
                                          whose L2 adds FP64 at the FP32 rate; at 1e8 photons

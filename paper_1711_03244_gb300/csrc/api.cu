@@ -107,7 +107,8 @@ __global__ void finalize_kernel(const double *bt, const unsigned long long *bs, 
 // The fluence map as accumulated, in the caller's type, optionally normalised to fluence
 // rate per launched photon (x inv_norm[label], inv_norm = 1 / (mua h^3 N dt)):
 //   accum 0: the FP32 map;  accum 2: the FP64 map;
-//   accum 1: hi + lo (+ the tile's FP64 sum inside the block tile), summed in FP64.
+//   accum 1: hi + lo of the interleaved pairs (+ the tile's FP64 sum inside the block
+//   tile), summed in FP64.
 struct TileBox {
     int lo[4], size[4];
 };
@@ -115,7 +116,7 @@ struct TileBox {
 // The maps and labels carry the walk's one-voxel border ([g][nz+2][ny+2][nx+2]); the
 // output is unpadded [g][nz][ny][nx].
 template <typename T>
-__global__ void resolve_kernel(int mode, const float *hi, const float *lo, const double *f64,
+__global__ void resolve_kernel(int mode, const float *hi, const double *f64,
                                TileBox tb, unsigned nx, unsigned ny, unsigned nvox, unsigned pnvox,
                                unsigned n_gates, const uint8_t *labels, const float *inv_norm,
                                T *out)
@@ -138,7 +139,7 @@ __global__ void resolve_kernel(int mode, const float *hi, const float *lo, const
         if (mode == 2) {
             d = f64[pi];
         } else {
-            d = (double)hi[pi] + (double)lo[pi];
+            d = (double)hi[2 * pi] + (double)hi[2 * pi + 1];     // interleaved (hi, lo)
             const unsigned tx = x - (unsigned)tb.lo[0], ty = y - (unsigned)tb.lo[1];
             const unsigned tz = z - (unsigned)tb.lo[2], tg = g - (unsigned)tb.lo[3];
             if (tx < (unsigned)tb.size[0] && ty < (unsigned)tb.size[1] &&
@@ -235,7 +236,7 @@ struct mcx_sim {
     bool source_set = false;
     std::vector<float> det;             // [n_det][4] cx, cy, cz, r (mm)
 
-    DevBuf labels, fluence, fluence_lo, fluence64, tables, detb, det_buf, exits, block_tally,
+    DevBuf labels, fluence, fluence64, tables, detb, det_buf, exits, block_tally,
         block_stats, ctrl, out, staging, inv_norm, sort_keys, sort_vals;
     int tile_lo[4] = {0, 0, 0, 0}, tile_size[4] = {0, 0, 0, 0};
     std::vector<unsigned char> host_tables;
@@ -539,9 +540,10 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     const uint64_t nvox = (uint64_t)(s->nx + 2) * (s->ny + 2) * (s->nz + 2);
     const uint64_t nflu = nvox * cfg->n_gates;
     const int stride = kRecBase + (int)s->n_media - 1;
-    MCX_CUDA(s, s->fluence.ensure(nflu * sizeof(float)), "allocating the fluence map");
+    // accum 1 keeps each voxel's (hi, lo) pair in adjacent words
+    const uint64_t nflu32 = accum == kAccCompensated ? 2 * nflu : nflu;
+    MCX_CUDA(s, s->fluence.ensure(nflu32 * sizeof(float)), "allocating the fluence map");
     if (accum == kAccCompensated) {
-        MCX_CUDA(s, s->fluence_lo.ensure(nflu * sizeof(float)), "allocating the fluence map");
         MCX_CUDA(s, s->fluence64.ensure((size_t)std::max(tile_e, 1) * sizeof(double)), "allocating the tile map");
     } else if (accum == kAccF64) {
         MCX_CUDA(s, s->fluence64.ensure(nflu * sizeof(double)), "allocating the FP64 fluence map");
@@ -576,7 +578,6 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     unsigned char *tbase = s->tables.as<unsigned char>();
     p.labels = s->labels.as<uint8_t>();
     p.fluence = s->fluence.as<float>();
-    p.fluence_lo = s->fluence_lo.as<float>();
     p.fluence64 = s->fluence64.as<double>();
     for (int a = 0; a < 4; ++a) {
         p.tile_lo[a] = tlo[a];
@@ -645,9 +646,8 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.claim_chunk = kClaimChunk;
 
     // zero the outputs, walk, reduce
-    zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu);
+    zero_words<<<grid_for(nflu32 / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu32);
     if (accum == kAccCompensated) {
-        zero_words<<<grid_for(nflu / 4 + 1), 256, 0, st>>>(s->fluence_lo.as<uint32_t>(), (size_t)nflu);
         zero_words<<<grid_for((size_t)tile_e / 2 + 1), 256, 0, st>>>(s->fluence64.as<uint32_t>(),
                                                                      (size_t)std::max(tile_e, 1) * 2);
     } else if (accum == kAccF64) {
@@ -767,7 +767,6 @@ static mcx_status read_fluence_t(mcx_sim *s, T *dst, uint64_t n_elems, int32_t n
         tb.size[a] = s->tile_size[a];
     }
     resolve_kernel<T><<<grid_for(n), 256, 0, st>>>(mode, s->fluence.as<float>(),
-                                                   s->fluence_lo.as<float>(),
                                                    s->fluence64.as<double>(), tb, s->nx, s->ny,
                                                    (unsigned)nvox, (unsigned)pnvox, s->cfg.n_gates,
                                                    s->labels.as<uint8_t>(), inv_dev, out);
@@ -891,7 +890,7 @@ void mcx_destroy(mcx_sim *s)
     if (!s) return;
     DeviceGuard g(s->device);
     if (s->ran) cudaEventSynchronize(s->ev_done);
-    for (DevBuf *b : {&s->labels, &s->fluence, &s->fluence_lo, &s->fluence64, &s->tables,
+    for (DevBuf *b : {&s->labels, &s->fluence, &s->fluence64, &s->tables,
                       &s->detb, &s->det_buf, &s->exits,
                       &s->block_tally, &s->block_stats, &s->ctrl, &s->out, &s->staging,
                       &s->inv_norm, &s->sort_keys, &s->sort_vals})

@@ -58,8 +58,8 @@ struct WalkParams {
     // side ([nz+2][ny+2][nx+2]) except in the allocation-free run, whose caller-owned
     // buffers are unpadded; nvox, sy and sz describe the layout actually used.
     const uint8_t *labels;            // [nz][ny][nx] (+ border)
-    float *fluence;                   // [n_gates][nvox] absorbed weight (accum 1: the hi part)
-    float *fluence_lo;                // accum 1: [n_gates][nvox] the lo part
+    float *fluence;                   // [n_gates][nvox] absorbed weight; accum 1: [n_gates][nvox][2]
+                                      // compensated (hi, lo) pairs, the two words adjacent
     double *fluence64;                // accum 2: [n_gates][nvox]; accum 1: the tile's FP64 map
     int tile_lo[4];                   // accum 1: tile origin (x, y, z, gate)
     int tile_size[4];                 // accum 1: tile extent; entries = product

@@ -388,7 +388,8 @@ walk_kernel(const WalkParams p)
                                        p.tile_size[0] + tx;
                     pair_add(s_hi + k, s_lo + k, float(acc));
                 } else {
-                    pair_add(p.fluence + idx, p.fluence_lo + idx, float(acc));
+                    // the map's (hi, lo) words are adjacent: both additions touch one sector
+                    pair_add(p.fluence + 2 * idx, p.fluence + 2 * idx + 1, float(acc));
                 }
             }
             ++c_flush;
