@@ -69,6 +69,12 @@ def test_argument_errors_before_device_work(lib):
     assert L.mcx_set_media(None, 1, None) == m.MCX_E_ARG
     assert L.mcx_run(None, None) == m.MCX_E_ARG
     assert L.mcx_debug_primitive(7, 1, None, None) == m.MCX_E_ARG
+    # the bordered device copy must stay below 2^32 voxels: 4094^2 x 256 does not
+    assert L.mcx_create_volume(ctypes.byref(h), 4094, 4094, 254, 1.0, lab, 0) == m.MCX_E_ARG
+    r = ctypes.c_double()
+    assert L.mcx_probe_rate(10, 0, ctypes.byref(r)) == m.MCX_E_ARG
+    assert L.mcx_probe_rate(-1, 0, ctypes.byref(r)) == m.MCX_E_ARG
+    assert L.mcx_probe_rate(0, 0, None) == m.MCX_E_ARG
     L.mcx_destroy(None)
 
 
