@@ -210,6 +210,8 @@ __device__ __forceinline__ R fresnel(R n1, R n2, R ci, R st2)
 // face ahead along that axis is one FMA on the in-voxel fraction q:
 //   u > 0: (1 - q) / u = fma(q, -inv, inv);   u < 0: -q / u = fma(q, -inv, 0)
 // i.e. fma(q, -inv, max(inv, 0)); u = 0 gives huge * (1 - q), never the nearest face.
+// A fraction that rounding pushed past its face gives a negative distance; the walk clamps
+// the nearest one to 0 (a zero-length step onto that face) after taking the minimum.
 template <typename R>
 __device__ __forceinline__ R inv_dir(R u)
 {
@@ -219,8 +221,7 @@ __device__ __forceinline__ R inv_dir(R u)
 template <typename R>
 __device__ __forceinline__ R face_dist(R q, R inv)
 {
-    const R d = fma(q, -inv, inv > R(0) ? inv : R(0));
-    return d > R(0) ? d : R(0);
+    return fma(q, -inv, inv > R(0) ? inv : R(0));
 }
 
 // ------------------------------------------------------------------------------ kernel
@@ -532,7 +533,6 @@ walk_kernel(const WalkParams p)
             }
             const MedA<R> A = medA(lab);
             // ---- a5: nearest face (lowest axis on ties), scattering point, time limit
-            // (a fraction that rounding pushed past its face gives a zero-length step)
             const R dxf = face_dist(qx, iux);
             const R dyf = face_dist(qy, iuy);
             const R dzf = face_dist(qz, iuz);
@@ -540,6 +540,7 @@ walk_kernel(const WalkParams p)
             int ax = 0;
             if (dyf < l) { l = dyf; ax = 1; }
             if (dzf < l) { l = dzf; ax = 2; }
+            l = l > R(0) ? l : R(0);          // rounding past a face: a zero-length step onto it
             int ev = EV_FACE;
             const R dscat = s * A.inv_mus;
             if (dscat <= l) { l = dscat; ev = EV_SCAT; }
