@@ -1,8 +1,8 @@
 // Learned 3-D denoiser for low-photon fluence maps: a small U-Net (3 levels, 16/32/64
 // channels, 3x3x3 convolutions) with BF16 weights and activations and FP32 accumulation,
-// trained and run by hand-written tensor-core kernels: the convolutions and their input
-// gradients on tcgen05 (TMA-fed shared-memory operands, accumulators in tensor memory),
-// the weight gradients on warp-level mma.sync m16n8k16.
+// trained and run by hand-written tensor-core kernels: the convolutions, their input
+// gradients and their weight gradients on tcgen05 (TMA-fed shared-memory operands,
+// accumulators in tensor memory).
 // The network stands in for photons: it maps the log-fluence of a low-photon run to the
 // log-fluence a high-photon run would give, and a plain high-photon run stays the
 // fallback.  (This extends the method; the paper has no counterpart.)
@@ -50,16 +50,6 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
     return *reinterpret_cast<const unsigned *>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
-                                         unsigned a3, unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 struct Vol {
     int n, d, h, w;               // batch, depth (z), height (y), width (x)
     __host__ __device__ long long pos() const { return (long long)n * d * h * w; }
@@ -82,8 +72,8 @@ struct Vol {
 // pattern -- the K-major SWIZZLE_32B operand layout (one row holds one MMA's K = 16;
 // 8-row groups 256 B apart), so a one-row shift of the operand is a 32-byte shift of its
 // start address (the swizzle follows absolute shared addresses).  Two 16-channel groups
-// per 32-byte row halve the TMA rows of the earlier 8-channel boxes.  conv3d_fwd_ws and
-// the weight gradient stage 8-channel boxes of 16-byte rows in the no-swizzle layout
+// per 32-byte row halve the TMA rows of the earlier 8-channel boxes.  conv3d_fwd_ws stages
+// 8-channel boxes of 16-byte rows in the no-swizzle layout
 // (8-row core matrices 128 B apart; chunks one leading-dimension offset apart).  A tile
 // takes 3 windows (one per plane); each feeds 9 taps x cin/16 tcgen05.mma instructions
 // (K = 16, N = COUT).
@@ -721,191 +711,222 @@ conv3d_fwd_ws(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     }
 }
 
-// Weight gradient: dW[tap][co][ci] = sum_p dY[p][co] X[p + off(tap)][ci], over the same
-// tiles and windows as the forward kernel (positions q along padded lines; the dY tile's
-// pad rows come in as zeros from the tensor map, so the windows' pad and neighbour rows
-// contribute nothing).  The GEMM per tap has M = cout (16 per fragment), N = cin (8 per
-// fragment) and K = the tile's 128 positions: too narrow in M for tcgen05 (M >= 64), so it
-// runs on warp-level mma.sync m16n8k16 with operands read from shared memory by
-// ldmatrix.trans (the staged rows are position-major, the fragments want the position
-// index along K).  One producer thread streams (dY tile, X window) stages by TMA; eight
-// consumer warps each own a fixed share of the (tap, m-fragment, n-fragment pair) units
-// and accumulate them in registers over every tile the CTA handles, then add them to dW
-// with FP32 atomics.  With many units per warp the taps are split over three CTA groups
-// (one per dz); each stage then carries only that plane's window.
-constexpr int kWgConsumers = 8, kWgThreads = 32 * (kWgConsumers + 1);
+// ------------------------------------------------------ weight gradient on tcgen05
+// dW[tap][co][ci] = sum_p dY[p][co] X[p + off(tap)][ci] as tcgen05 GEMMs whose reduction
+// (K) runs over positions q, numbered along padded lines as in the forward kernel.  The
+// taps are stacked into the MMA's two free dimensions by shifted reads of staged windows,
+// both read MN-major (channels contiguous) in the 32-byte swizzle:
+//   M = (a, ci), a = dx + 1: the X window, one 16-channel atom per a, atoms one 32-byte
+//       row apart, so atom a reads the row a positions further on (a = 0..3, M = 64; the
+//       products of a = 3 are computed and discarded);
+//   N = (j, co), j = 1 - dy: the dY window, atoms one padded line (PW rows) apart.
+// For K index b, atom pair (a, j) multiplies X[b - PW - 1 + a] with dY[b + (j - 2) PW]:
+// the tap (dy, dx) = (1 - j, a - 1) at dY position p = b + (j - 2) PW.  A plane's K range
+// runs over (h + 2) padded lines, so every shift j covers each position of the plane
+// exactly once; rows outside the volume come in as zeros from the tensor maps'
+// out-of-bounds fill (pad columns, lines and planes outside) and add nothing.  One MMA of
+// M = 64, N = 48, K = 16 thus forms 9 taps x 16 x 16 products, 3/4 of its rows useful.
+//
+// Work units are columns of up to zc planes at one q0, as in the forward kernel.  A stage
+// holds the X and dY windows of one plane w = z0 - 1 .. z0 + nz (dY only for the unit's
+// own planes); the MMAs of stage w form the dz = 0 product X_w dY_w and, with the
+// previous stage's windows, the dz = +1 product X_w dY_(w-1) and the dz = -1 product
+// X_(w-1) dY_w.  A stage is released once the next one's MMAs are issued, so each plane's
+// windows are loaded once per unit.  A CTA handles one pair of 16-channel groups (cin
+// group, cout group) and sums the three dz products over all its units in tensor memory
+// (3 x 48 of 256 allocated columns); after its last MMA the four warps read them out and
+// add them to dW with FP32 atomics.  Warp 0 lane 0 issues the TMA loads, warp 1 lane 0
+// the MMAs; every wait is bounded.
+constexpr int kWtThreads = 128, kWtM = 64, kWtN = 48, kWtCols = 256, kWtHeader = 1024;
 
-__host__ __device__ constexpr int wg_units_per_warp(int cin, int cout)
-{
-    return (9 * (cout / 16) * (cin / 16) + kWgConsumers - 1) / kWgConsumers;
-}
-// dz groups over CTAs: 1 (a CTA handles all 27 taps) when its accumulators fit in 96
-// registers, else 3
-__host__ __device__ constexpr int wg_groups(int cin, int cout) { return 3 * wg_units_per_warp(cin, cout) * 8 <= 96 ? 1 : 3; }
-__host__ __device__ constexpr int wg_dy_lines(int w) { return (127 + w + 1) / (w + 2) + 1; }
-__host__ __device__ constexpr int wg_lbo_dy(int w) { return ((wg_dy_lines(w) * (w + 2) * 16 + 127) / 128) * 128; }
-__host__ __device__ constexpr int wg_stage_bytes(int cin, int cout, int w)
-{
-    return (cout / 8) * wg_lbo_dy(w) + (cin / 8) * tc_lbo_a(w);
-}
-__host__ __device__ constexpr int wg_smem_bytes(int cin, int cout, int w, int ns)
-{
-    return 1024 + kTcHeader + ns * wg_stage_bytes(cin, cout, w);
-}
-__host__ __device__ constexpr int wg_stages(int cin, int cout, int w)
+// lines of a window: X rows from q0 - PW - 1 through q0 - PW + 129, dY rows from
+// q0 - 2 PW through q0 + 127
+__host__ __device__ constexpr int wt_xlines(int w) { return 130 / (w + 2) + 2; }
+__host__ __device__ constexpr int wt_ylines(int w) { return 127 / (w + 2) + 4; }
+// a window in shared memory: its lines of PW 32-byte rows plus 2 KiB that no load writes
+// (a bound on any read past the window), rounded to 1 KiB (swizzle atoms stay aligned)
+__host__ __device__ constexpr int wt_win_bytes(int lines, int w) { return ((lines * (w + 2) * 32 + 2048 + 1023) / 1024) * 1024; }
+__host__ __device__ constexpr int wt_stage_bytes(int w) { return wt_win_bytes(wt_xlines(w), w) + wt_win_bytes(wt_ylines(w), w); }
+__host__ __device__ constexpr int wt_smem_bytes(int w, int ns) { return 1024 + kWtHeader + ns * wt_stage_bytes(w); }
+// ring depth: 3-6 stages within the budget for two CTAs per SM, else 2-4 within one SM
+__host__ __device__ constexpr int wt_stages(int w)
 {
     for (int ns = 6; ns >= 3; --ns)
-        if (wg_smem_bytes(cin, cout, w, ns) <= kTcSmemBudget) return ns;
+        if (wt_smem_bytes(w, ns) <= kTcSmemBudget) return ns;
     for (int ns = 4; ns >= 2; --ns)
-        if (wg_smem_bytes(cin, cout, w, ns) <= kTcSmemMax) return ns;
+        if (wt_smem_bytes(w, ns) <= kTcSmemMax) return ns;
     return 0;
 }
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+// shared-memory descriptor of an MN-major operand in the 32-byte swizzle (layout type 6):
+// atoms of 16 MN elements x 8 K rows (rows of 32 B); lbo = byte stride between atoms along
+// MN, sbo = byte stride between 8-row groups along K
+__device__ __forceinline__ uint64_t sw32_mn_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr) : "memory");
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (6ull << 61);
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kWgThreads)
-conv3d_wgrad(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy, Vol v, int ns,
-             float *__restrict__ dW, unsigned *err)
+__global__ void __launch_bounds__(kWtThreads)
+conv3d_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy, Vol v, int ns,
+                int zc, float *__restrict__ dW, unsigned *err)
 {
-    constexpr int MT = COUT / 16, NP = CIN / 16, U = 9 * MT * NP, UPW = wg_units_per_warp(CIN, COUT);
-    constexpr int G = wg_groups(CIN, COUT), DZN = 3 / G;          // planes (dz) per CTA
+    constexpr int NG = COUT / 16;
+    // kind::f16, M = 64, N = 48, A and B both MN-major (bits 15 and 16)
+    constexpr uint32_t IDESC = idesc_bf16_f32(kWtM, kWtN) | (1u << 15) | (1u << 16);
     extern __shared__ unsigned char smem_raw[];
-    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-    const uint32_t full0 = base, empty0 = base + 64;
-    const int PW = v.w + 2, Lx = tc_lines(v.w), Ly = wg_dy_lines(v.w);
-    const int lbo_x = tc_lbo_a(v.w), lbo_y = wg_lbo_dy(v.w);
-    const int y_bytes = (COUT / 8) * lbo_y, stage_bytes = wg_stage_bytes(CIN, COUT, v.w);
-    const uint32_t ring = base + kTcHeader;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;      // 1 KiB aligned
+    // header: full[ns] at 0, empty[ns] at 64, MMA drain barrier at 128, TMEM address at 192
+    const uint32_t full0 = base, empty0 = base + 64, drain = base + 128;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_raw + (base + 192 - smem_u32(smem_raw)));
+    const int cig = (int)blockIdx.y / NG, cog = (int)blockIdx.y % NG;
+    const int PW = v.w + 2, Lx = wt_xlines(v.w), Ly = wt_ylines(v.w);
+    const int xbytes = wt_win_bytes(Lx, v.w), stage_bytes = wt_stage_bytes(v.w);
+    const uint32_t ring = base + kWtHeader;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int dz0 = G == 1 ? 0 : (int)blockIdx.y;                  // first plane index (0..2)
-    const int tiles_plane = (v.h * PW + kTcRows - 1) / kTcRows;
-    const int n_tiles = v.n * v.d * tiles_plane;
-    const int my_tiles = n_tiles > (int)blockIdx.x ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int n_steps = my_tiles * DZN;
-    struct Tl { int b, z, q0; };
-    auto tile_of = [&](int t) {
-        const int tile = (int)blockIdx.x + t * (int)gridDim.x;
-        const int plane = tile / tiles_plane;
-        return Tl{plane / v.d, plane % v.d, (tile % tiles_plane) * kTcRows};
+    // work units: columns of up to zc planes at one q0 over the extended plane
+    const int tiles_plane = ((v.h + 2) * PW + kTcRows - 1) / kTcRows;
+    const int cols_z = (v.d + zc - 1) / zc;
+    const int n_units = v.n * cols_z * tiles_plane;
+    const int my_units = n_units > (int)blockIdx.x ? (n_units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    struct Unit { int b, z0, nz, q0; };
+    auto unit_of = [&](int j) {
+        const int u = (int)blockIdx.x + j * (int)gridDim.x;
+        const int k = u % tiles_plane, r = u / tiles_plane;
+        const int z0 = (r % cols_z) * zc;
+        return Unit{r / cols_z, z0, min(zc, v.d - z0), k * kTcRows};
     };
-    auto first_line = [&](int q0) { return (q0 >= 1 ? (q0 - 1) / PW : -1) - 1; };
+    // first window lines (floor division): X from row q0 - PW - 1, dY from row q0 - 2 PW
+    auto x_line = [&](int q0) { const int r = q0 - PW - 1; return r >= 0 ? r / PW : -((PW - 1 - r) / PW); };
+    auto y_line = [&](int q0) { return q0 / PW - 2; };
 
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     ::"r"(smem_u32(tslot)), "r"(kWtCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
     if (tid == 0) {
         for (int b = 0; b < ns; ++b) {
             mbar_init(full0 + 8 * b, 1);
-            mbar_init(empty0 + 8 * b, kWgConsumers);
+            mbar_init(empty0 + 8 * b, 1);
         }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
     bool ok = true;
 
-    if (warp == kWgConsumers) {
-        // ------------------------------------------------------------ producer (TMA)
+    if (warp == 0) {
         if (lane == 0) {
-            const uint32_t tx = (COUT / 8) * (Ly * PW * 16) + (CIN / 8) * (Lx * PW * 16);
+            // -------------------------------------------------------- producer (TMA)
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmx)) : "memory");
+            asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&tmdy)) : "memory");
+            const uint32_t txx = (uint32_t)(Lx * PW * 32), txy = (uint32_t)(Ly * PW * 32);
             int b = 0, use = 0;
-            for (int s = 0; s < n_steps && ok; ++s) {
-                if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
-                if (!ok) break;
-                const Tl T = tile_of(s / DZN);
-                const int dz = dz0 + s % DZN - 1;
-                const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
-                mbar_expect_tx(fb, tx);
-                for (int c = 0; c < COUT / 8; ++c)
-                    tma_load_5d(st + c * lbo_y, &tmdy, 8 * c, -1, T.q0 / PW, T.z, T.b, fb);
-                for (int c = 0; c < CIN / 8; ++c)
-                    tma_load_5d(st + y_bytes + c * lbo_x, &tmx, 8 * c, -1, first_line(T.q0), T.z + dz, T.b, fb);
-                if (++b == ns) { b = 0; ++use; }
+            for (int uj = 0; uj < my_units && ok; ++uj) {
+                const Unit U = unit_of(uj);
+                const int xl = x_line(U.q0), yl = y_line(U.q0);
+                for (int j = 0; j < U.nz + 2 && ok; ++j) {     // plane z0 - 1 + j
+                    const bool hasy = j >= 1 && j <= U.nz;
+                    if (use > 0) ok &= mbar_wait(empty0 + 8 * b, (uint32_t)((use - 1) & 1));
+                    if (!ok) break;
+                    const uint32_t st = ring + b * stage_bytes, fb = full0 + 8 * b;
+                    mbar_expect_tx(fb, txx + (hasy ? txy : 0u));
+                    tma_load_5d(st, &tmx, 16 * cig, -1, xl, U.z0 - 1 + j, U.b, fb);
+                    if (hasy) tma_load_5d(st + xbytes, &tmdy, 16 * cog, -1, yl, U.z0 - 1 + j, U.b, fb);
+                    if (++b == ns) { b = 0; ++use; }
+                }
             }
-            for (int bb = 0; bb < ns; ++bb) {                 // every load has landed
+            // every load issued has landed before the CTA may exit
+            for (int bb = 0; bb < ns; ++bb) {
                 const int issued = use + (bb < b ? 1 : 0);
                 if (issued > 0) ok &= mbar_wait(full0 + 8 * bb, (uint32_t)((issued - 1) & 1));
             }
         }
-    } else {
-        // ------------------------------------------------------------ consumers (mma.sync)
-        float acc[DZN][UPW][2][4];
-#pragma unroll
-        for (int a = 0; a < DZN; ++a)
-#pragma unroll
-            for (int u = 0; u < UPW; ++u)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) acc[a][u][h][0] = acc[a][u][h][1] = acc[a][u][h][2] = acc[a][u][h][3] = 0.f;
-        // ldmatrix row addresses: lane l serves row l % 8 of matrix l / 8
-        const int mrow = (lane & 7) + ((lane >> 4) << 3);      // + 8 for matrices 2, 3 (A)
-        const int mcol = (lane >> 3) & 1;                      // chunk + 1 for matrices 1, 3 (A)
-        const int brow = (lane & 7) + (((lane >> 3) & 1) << 3); // + 8 for matrices 1, 3 (B)
-        const int bcol = lane >> 4;                            // chunk + 1 for matrices 2, 3 (B)
-        int b = 0, use = 0;
-        for (int s = 0; s < n_steps && ok; ++s) {
-            ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            const Tl T = tile_of(s / DZN);
-            const int dzl = s % DZN;
-            const uint32_t Ys = ring + b * stage_bytes, Xs = Ys + y_bytes;
-            const int offy = T.q0 - (T.q0 / PW) * PW, offx = T.q0 - first_line(T.q0) * PW;
-#pragma unroll
-            for (int dzc = 0; dzc < DZN; ++dzc) {
-                if (dzc != dzl) continue;                      // registers indexed statically
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // -------------------------------------------------------- MMA issuer
+            int started = 0;                                    // bit dz + 1: accumulator written
+            auto mma = [&](int dzi, uint64_t ad, uint64_t bd) {
+                const uint32_t accum = (uint32_t)((started >> dzi) & 1);
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem + (uint32_t)(dzi * kWtN)), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum)
+                             : "memory");
+                started |= 1 << dzi;
+            };
+            const uint32_t xlbo = 32, ylbo = (uint32_t)(PW * 32), sbo = 256;
+            int b = 0, use = 0, bp = 0;
+            for (int uj = 0; uj < my_units && ok; ++uj) {
+                const Unit U = unit_of(uj);
+                // window rows of K index q0
+                const uint32_t rx = (uint32_t)(U.q0 - PW - 1 - x_line(U.q0) * PW) * 32;
+                const uint32_t ry = (uint32_t)(U.q0 % PW) * 32;
+                for (int j = 0; j < U.nz + 2 && ok; ++j) {
+                    ok &= mbar_wait(full0 + 8 * b, (uint32_t)(use & 1));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const bool hasy = j >= 1 && j <= U.nz, prevy = j >= 2;
+                    const uint32_t xs = ring + b * stage_bytes, xp = ring + bp * stage_bytes;
+                    const uint32_t ys = xs + xbytes, yp = xp + xbytes;
 #pragma unroll 1
-                for (int ks = 0; ks < 8; ++ks) {
-                    unsigned af[MT][4];
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-                        ldsm_x4_t(Ys + (2 * mt + mcol) * lbo_y + (offy + 16 * ks + mrow) * 16,
-                                  af[mt][0], af[mt][1], af[mt][2], af[mt][3]);
-#pragma unroll
-                    for (int j = 0; j < UPW; ++j) {
-                        const int u = warp + kWgConsumers * j;
-                        if (u >= U) break;
-                        const int t9 = u / (MT * NP), mt = (u / NP) % MT, np = u % NP;
-                        unsigned b0, b1, b2, b3;
-                        const int toff = (t9 / 3 - 1) * PW + (t9 % 3 - 1);   // (dy, dx) row shift
-                        ldsm_x4_t(Xs + (2 * np + bcol) * lbo_x + (offx + toff + 16 * ks + brow) * 16, b0, b1, b2, b3);
-                        unsigned a0 = af[0][0], a1 = af[0][1], a2 = af[0][2], a3 = af[0][3];
-#pragma unroll
-                        for (int m = 1; m < MT; ++m)
-                            if (m == mt) { a0 = af[m][0]; a1 = af[m][1]; a2 = af[m][2]; a3 = af[m][3]; }
-                        mma_bf16(acc[dzc][j][0], a0, a1, a2, a3, b0, b1);
-                        mma_bf16(acc[dzc][j][1], a0, a1, a2, a3, b2, b3);
+                    for (int kk = 0; kk < kTcRows / 16; ++kk) {
+                        const uint32_t ko = (uint32_t)(kk * 16 * 32);
+                        const uint64_t ax = sw32_mn_desc(xs + rx + ko, xlbo, sbo);
+                        if (hasy) {
+                            const uint64_t ay = sw32_mn_desc(ys + ry + ko, ylbo, sbo);
+                            mma(1, ax, ay);                                          // dz = 0
+                            mma(0, sw32_mn_desc(xp + rx + ko, xlbo, sbo), ay);         // dz = -1
+                        }
+                        if (prevy) mma(2, ax, sw32_mn_desc(yp + ry + ko, ylbo, sbo));  // dz = +1
                     }
+                    if (j >= 1) tc_commit(empty0 + 8 * bp);             // the previous plane is done
+                    if (j == U.nz + 1) tc_commit(empty0 + 8 * b);       // and so is the unit's last
+                    bp = b;
+                    if (++b == ns) { b = 0; ++use; }
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8 * b);
-            if (++b == ns) { b = 0; ++use; }
+            // every MMA issued has completed before the read-out or the release of tensor
+            // memory, also when a wait above gave up
+            tc_commit(drain);
+            ok &= mbar_wait(drain, 0);
         }
-        // add this CTA's sums to dW[tap][co][ci]
-        if (ok && my_tiles) {
-            const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-            for (int dzc = 0; dzc < DZN; ++dzc)
-#pragma unroll
-                for (int j = 0; j < UPW; ++j) {
-                    const int u = warp + kWgConsumers * j;
-                    if (u >= U) break;
-                    const int t9 = u / (MT * NP), mt = (u / NP) % MT, np = u % NP;
-                    const int tap = 9 * (dz0 + dzc) + t9;
-                    float *w = dW + (size_t)tap * COUT * CIN;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int ci = 16 * np + 8 * h + 2 * t, co = 16 * mt + g;
-                        atomicAdd(w + (size_t)co * CIN + ci, acc[dzc][j][h][0]);
-                        atomicAdd(w + (size_t)co * CIN + ci + 1, acc[dzc][j][h][1]);
-                        atomicAdd(w + (size_t)(co + 8) * CIN + ci, acc[dzc][j][h][2]);
-                        atomicAdd(w + (size_t)(co + 8) * CIN + ci + 1, acc[dzc][j][h][3]);
-                    }
-                }
-        }
+        __syncwarp();
     }
-    if (!__syncthreads_and(ok) && tid == 0) atomicOr(err, 1u);
+    const bool all_ok = __syncthreads_and(ok);
+    if (all_ok && my_units > 0) {
+        // ------------------------------------------------------------ read-out
+        tc_fence_after();
+        // accumulator row r = 16 a + ci (M = 64) sits in TMEM lane 32 (r / 16) + r % 16
+        const int a = warp, ci = lane;
+        const bool row = lane < 16 && warp < 3;
+#pragma unroll 1
+        for (int dzi = 0; dzi < 3; ++dzi)
+#pragma unroll 1
+            for (int jn = 0; jn < 3; ++jn) {
+                float acc[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dzi * kWtN + jn * 16), acc);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (row) {
+                    const int tap = 9 * dzi + 3 * (2 - jn) + a;          // (dz, dy, dx) + 1
+                    float *w = dW + ((size_t)tap * COUT + 16 * cog) * CIN + 16 * cig + ci;
+#pragma unroll
+                    for (int co = 0; co < 16; ++co) atomicAdd(w + (size_t)co * CIN, acc[co]);
+                }
+            }
+    }
+    if (!all_ok && tid == 0) atomicOr(err, 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kWtCols) : "memory");
+    }
 }
 
 // ------------------------------------------------------------------------ elementwise
@@ -1371,41 +1392,50 @@ cudaError_t launch_fwd_tc(const bf16 *X, int cin, const bf16 *W, const float *bi
 }
 
 template <int CIN, int COUT>
-cudaError_t launch_wg_t(const bf16 *X, const bf16 *dY, Vol v, float *dW, unsigned *err, cudaStream_t st)
+cudaError_t launch_wt_t(const bf16 *X, const bf16 *dY, Vol v, float *dW, unsigned *err, cudaStream_t st)
 {
-    if (v.w + 2 > 256 || tc_lines(v.w) > 256) return cudaErrorInvalidValue;
+    if (v.w + 2 > 256 || wt_ylines(v.w) > 256) return cudaErrorInvalidValue;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
+    // 16-channel boxes of whole padded lines (from x = -1), 32-byte swizzle
     CUtensorMap mx, my;
     const cuuint32_t one[5] = {1, 1, 1, 1, 1};
     auto map5 = [&](CUtensorMap *m, const bf16 *ptr, int c, int lines) {
         const cuuint64_t dim[5] = {(cuuint64_t)c, (cuuint64_t)v.w, (cuuint64_t)v.h, (cuuint64_t)v.d, (cuuint64_t)v.n};
         const cuuint64_t str[4] = {(cuuint64_t)c * 2, (cuuint64_t)v.w * c * 2, (cuuint64_t)v.h * v.w * c * 2,
                                    (cuuint64_t)v.d * v.h * v.w * c * 2};
-        const cuuint32_t box[5] = {8, (cuuint32_t)(v.w + 2), (cuuint32_t)lines, 1, 1};
+        const cuuint32_t box[5] = {16, (cuuint32_t)(v.w + 2), (cuuint32_t)lines, 1, 1};
         return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(ptr), dim, str, box, one,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    if (!map5(&mx, X, CIN, tc_lines(v.w)) || !map5(&my, dY, COUT, wg_dy_lines(v.w))) return cudaErrorInvalidValue;
-    const int ns = wg_stages(CIN, COUT, v.w);
+    if (!map5(&mx, X, CIN, wt_xlines(v.w)) || !map5(&my, dY, COUT, wt_ylines(v.w))) return cudaErrorInvalidValue;
+    const int ns = wt_stages(v.w);
     if (ns < 2) return cudaErrorInvalidValue;
-    const int smem = wg_smem_bytes(CIN, COUT, v.w, ns);
-    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int smem = wt_smem_bytes(v.w, ns);
+    cudaError_t e = cudaFuncSetAttribute(conv3d_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, smem_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
         return e;
-    constexpr int G = wg_groups(CIN, COUT);
-    const int per_sm = std::max(1, std::min(smem_sm / (smem + 1024), 2048 / kWgThreads));
-    const long long tiles = (long long)v.n * v.d * ((v.h * (v.w + 2) + kTcRows - 1) / kTcRows);
-    if (tiles * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
-    // CTAs per group: every resident slot, but at least 4 tiles each (the final atomics)
-    const long long per_group = std::max<long long>(1, std::min<long long>((tiles + 3) / 4, (long long)sms * per_sm / G));
-    const dim3 grid((unsigned)per_group, G);
-    conv3d_wgrad<CIN, COUT><<<grid, kWgThreads, smem, st>>>(mx, my, v, ns, dW, err);
+    // resident CTAs per SM: shared memory (1 KiB per CTA reserved by the system), tensor
+    // memory (512 columns), threads
+    const int per_sm = std::max(1, std::min({smem_sm / (smem + 1024), 512 / kWtCols, 2048 / kWtThreads}));
+    const long long tiles_plane = ((long long)(v.h + 2) * (v.w + 2) + kTcRows - 1) / kTcRows;
+    if ((long long)v.n * v.d * tiles_plane * 3 >= (1LL << 31)) return cudaErrorInvalidValue;
+    constexpr int pairs = (CIN / 16) * (COUT / 16);
+    const long long slots = (long long)sms * per_sm;
+    // column depth: the deepest of 16, 8, 4, 2 that leaves 2 units per resident CTA, else 1
+    int zc = 1;
+    for (int z = 16; z >= 2; z /= 2)
+        if ((long long)v.n * ((v.d + z - 1) / z) * tiles_plane * pairs >= 2 * slots) { zc = z; break; }
+    zc = std::min(zc, v.d);
+    const long long units = (long long)v.n * ((v.d + zc - 1) / zc) * tiles_plane;
+    const long long per_pair = std::max<long long>(1, std::min<long long>(units, std::max<long long>(1, slots / pairs)));
+    const dim3 grid((unsigned)per_pair, (unsigned)pairs);
+    conv3d_wgrad_tc<CIN, COUT><<<grid, kWtThreads, smem, st>>>(mx, my, v, ns, zc, dW, err);
     return cudaGetLastError();
 }
 
@@ -1415,7 +1445,7 @@ cudaError_t launch_bwd_w(const bf16 *X, int cin, const bf16 *dY, int cout, Vol v
                          cudaStream_t st)
 {
 #define MCX_WG(ci, co) \
-    if (cin == ci && cout == co) return launch_wg_t<ci, co>(X, dY, v, dW, err, st);
+    if (cin == ci && cout == co) return launch_wt_t<ci, co>(X, dY, v, dW, err, st);
     MCX_WG(16, 16) MCX_WG(16, 32) MCX_WG(32, 32) MCX_WG(32, 64) MCX_WG(64, 64) MCX_WG(96, 32) MCX_WG(48, 16)
 #undef MCX_WG
     return cudaErrorInvalidValue;

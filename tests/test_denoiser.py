@@ -119,6 +119,30 @@ def test_conv_weight_gradient_matches_oracle(g, cin, cout):
     assert rel < 1e-5
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 16), (48, 16), (32, 64)])
+def test_conv_weight_gradient_large_ragged_columns(g, cin, cout):
+    """a volume with multi-plane work units, a depth (19) that leaves a ragged last column,
+    lines (40) that end inside a tile, and several CTAs per channel-group pair"""
+    import torch
+    rng = np.random.default_rng(400 + cin + 7 * cout)
+    x = bf16(rng.normal(size=(2, 19, 40, 64, cin)).astype(np.float32))
+    dy = bf16(rng.normal(size=(2, 19, 40, 64, cout)).astype(np.float32))
+    got = g.mcx_debug_conv3d(1, x, dy=dy).astype(np.float64)
+    ref = np.zeros_like(got)
+    s_abs = np.zeros_like(got)
+    for t, (dz, dyy, dx) in enumerate(od.tap_offsets()):
+        xs = od.shift(torch.tensor(x), dz, dyy, dx).numpy()
+        ref[t] = np.einsum("nzyxo,nzyxc->oc", dy, xs, optimize=True)
+        s_abs[t] = np.einsum("nzyxo,nzyxc->oc", np.abs(dy), np.abs(xs), optimize=True)
+    P = x.shape[0] * x.shape[1] * x.shape[2] * x.shape[3]
+    bound = P * 2.0 ** -22 * s_abs
+    err = np.abs(got - ref)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"dW {cin}x{cout} on 2x19x40x64: rel L2 {rel:.2e}, max err/bound {np.max(err / bound):.2f}")
+    assert np.all(err <= bound)
+    assert rel < 1e-5
+
+
 def _net(g, shape, n, params, n_aux=0):
     d = g.Denoiser(shape, max_batch=n, seed=1, n_aux=n_aux)
     d.set_params(params)
