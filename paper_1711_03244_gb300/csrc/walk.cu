@@ -356,6 +356,12 @@ walk_kernel(const WalkParams p)
     R w = 0, t = 0, s = 0, absorbed = 0, Lcur = 0, acc = 0;
     unsigned gate = 0;            // time gate of the current deposit run
     R t_next = 0;                 // time at which the gate advances
+    // the current medium's segment constants, reloaded only when the label changes (kept in
+    // registers: measured 5% faster at C2 than a shared-memory lookup in every segment); the
+    // compensated mode, whose block tile needs those registers, looks them up per segment
+    constexpr bool KEEP_MED = ACC != kAccCompensated;
+    MedA<R> A_cur{};
+    R tpl_cur = 0;                // its time per unit length
     unsigned nscat = 0, nrr = 0, c_face = 0, c_fres = 0, c_flush = 0, c_rr = 0;
     float Lpath[DET ? kMaxDetMedia : 1];
 
@@ -494,6 +500,10 @@ walk_kernel(const WalkParams p)
                         vlin = inside ? ((unsigned)iz * G_sz + (unsigned)iy * G_sy + (unsigned)ix +
                                          (PAD ? G_sz + G_sy + 1u : 0u)) : 0u;
                         lab = inside ? (int)__ldg(G_labels + vlin) : 0;
+                        if constexpr (KEEP_MED) {
+                            A_cur = medA(lab);
+                            tpl_cur = med_tpl(lab);
+                        }
                         alive = lab != 0;
                         if (alive) {
                             new_hop();
@@ -532,7 +542,8 @@ walk_kernel(const WalkParams p)
                 gate = g2 < last_gate ? g2 : last_gate;
                 t_next = gate < last_gate ? R(gate + 1u) * C.dt : M<R>::huge();
             }
-            const MedA<R> A = medA(lab);
+            const MedA<R> A = KEEP_MED ? A_cur : medA(lab);
+            const R tpl = KEEP_MED ? tpl_cur : med_tpl(lab);
             // ---- a5: nearest face (lowest axis on ties), scattering point, time limit
             const R dxf = face_dist(qx, iux);
             const R dyf = face_dist(qy, iuy);
@@ -552,7 +563,7 @@ walk_kernel(const WalkParams p)
             qx += l * ux;
             qy += l * uy;
             qz += l * uz;
-            t += l * med_tpl(lab);
+            t += l * tpl;
             s -= l * A.mus;                   // a scattering event draws the next hop
             if (DET) Lcur += l;
             const R wn = w * M<R>::attenuation(A.mua, l);
@@ -654,6 +665,10 @@ walk_kernel(const WalkParams p)
                             Lcur = R(0);
                         }
                         lab = b;
+                        if constexpr (KEEP_MED) {
+                            A_cur = medA(b);
+                            tpl_cur = med_tpl(b);
+                        }
                     }
                     if (escape) fate = MCX_FATE_ESCAPED;
                     else if (s <= R(0)) new_hop();        // hop used up by rounding at the face
