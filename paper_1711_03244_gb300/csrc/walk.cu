@@ -173,6 +173,15 @@ __device__ __forceinline__ void hg_sample(const MedB<R> &B, R xi, R &ct, R &st)
     st = M<R>::sqrt(omc * opc);
 }
 
+// The Henyey-Greenstein constants of anisotropy g; the host's table rounds them alike
+// (1 - g^2 as one fused multiply-add), so a walk that derives them from a g kept in a
+// register follows the same trajectories as one that reads the table.
+template <typename R>
+__host__ __device__ __forceinline__ MedB<R> hg_consts(R g)
+{
+    return MedB<R>{R(1) - g, R(1) + g, fma(-g, g, R(1)), g + g};
+}
+
 // MCML rotation of unit vector u by deflection (cos ct, sin st) and azimuth (sp, cp).
 template <typename R>
 __device__ __forceinline__ void rotate(R &ux, R &uy, R &uz, R ct, R st, R sp, R cp)
@@ -362,6 +371,7 @@ walk_kernel(const WalkParams p)
     constexpr bool KEEP_MED = ACC != kAccCompensated;
     MedA<R> A_cur{};
     R tpl_cur = 0;                // its time per unit length
+    R g_cur = 0;                  // its anisotropy (the scattering constants follow from it)
     unsigned nscat = 0, nrr = 0, c_face = 0, c_fres = 0, c_flush = 0, c_rr = 0;
     float Lpath[DET ? kMaxDetMedia : 1];
 
@@ -503,6 +513,7 @@ walk_kernel(const WalkParams p)
                         if constexpr (KEEP_MED) {
                             A_cur = medA(lab);
                             tpl_cur = med_tpl(lab);
+                            g_cur = R(0.5) * medB(lab).two_g;      // 2g / 2: exact
                         }
                         alive = lab != 0;
                         if (alive) {
@@ -668,6 +679,7 @@ walk_kernel(const WalkParams p)
                         if constexpr (KEEP_MED) {
                             A_cur = medA(b);
                             tpl_cur = med_tpl(b);
+                            g_cur = R(0.5) * medB(b).two_g;
                         }
                     }
                     if (escape) fate = MCX_FATE_ESCAPED;
@@ -676,7 +688,7 @@ walk_kernel(const WalkParams p)
             } else {
                 // ---- a10: Henyey-Greenstein scattering; a11: Russian roulette
                 ++nscat;
-                const MedB<R> B = medB(lab);
+                const MedB<R> B = KEEP_MED ? hg_consts(g_cur) : medB(lab);
                 float u_hop, xi_hg, xi_phi;
                 rng.triple(u_hop, xi_hg, xi_phi);
                 R ct, st;
@@ -811,8 +823,7 @@ __global__ void primitive_kernel(int kind, uint64_t n, const float *in, float *o
     if (i >= n) return;
     if (kind == 0) {
         const float g = in[2 * i], xi = in[2 * i + 1];
-        MedB<float> B;
-        B.one_m_g = 1.f - g; B.one_p_g = 1.f + g; B.one_m_g2 = 1.f - g * g; B.two_g = 2.f * g;
+        const MedB<float> B = hg_consts(g);
         float ct, st;
         hg_sample(B, xi, ct, st);
         out[2 * i] = ct;
@@ -862,11 +873,7 @@ void fill(int n_media, const float *props, float h, unsigned char *buf, const vo
         A.inv_mus = mus_v > 0 ? R(M<R>::kHopUnit / mus_v) : R(INFINITY);
         A.mua = R(mua_v * M<R>::kAbsScale);
         A.len_per_t = c0 / (nn * hh);
-        MedB<R> B;
-        B.one_m_g = R(1) - g;
-        B.one_p_g = R(1) + g;
-        B.one_m_g2 = R(1) - g * g;
-        B.two_g = R(2) * g;
+        const MedB<R> B = hg_consts(g);
         reinterpret_cast<MedA<R> *>(buf + a)[m] = A;
         reinterpret_cast<MedB<R> *>(buf + b)[m] = B;
         reinterpret_cast<R *>(buf + n)[m] = nn;
