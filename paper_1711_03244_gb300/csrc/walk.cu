@@ -362,7 +362,9 @@ walk_kernel(const WalkParams p)
     int ix = 0, iy = 0, iz = 0, lab = 0;
     unsigned vlin = 0;
     R qx = 0, qy = 0, qz = 0, ux = 0, uy = 0, uz = 1, iux = 0, iuy = 0, iuz = 0;
-    R w = 0, t = 0, s = 0, absorbed = 0, Lcur = 0, acc = 0;
+    // gained: the photon's roulette gains; its absorbed weight is 1 + gained - (its final
+    // weight), since absorption and roulette are the only changes of w
+    R w = 0, t = 0, s = 0, gained = 0, Lcur = 0, acc = 0;
     unsigned gate = 0;            // time gate of the current deposit run
     R t_next = 0;                 // time at which the gate advances
     // the current medium's segment constants, reloaded only when the label changes (kept in
@@ -498,7 +500,7 @@ walk_kernel(const WalkParams p)
                         iz = (int)fz - ((pz == fz && uz < R(0)) ? 1 : 0);
                         qx = px - R(ix); qy = py - R(iy); qz = pz - R(iz);
                         iux = inv_dir(ux); iuy = inv_dir(uy); iuz = inv_dir(uz);
-                        w = R(1); t = R(0); absorbed = R(0); Lcur = R(0); acc = R(0);
+                        w = R(1); t = R(0); gained = R(0); Lcur = R(0); acc = R(0);
                         gate = 0;
                         t_next = last_gate > 0 ? C.dt : M<R>::huge();
                         nscat = nrr = c_face = c_fres = c_flush = c_rr = 0;
@@ -580,7 +582,6 @@ walk_kernel(const WalkParams p)
             const R wn = w * M<R>::attenuation(A.mua, l);
             const R dw = w - wn;
             w = wn;
-            absorbed += dw;
             acc += dw;
 
             if (ev == EV_TIME) {
@@ -704,6 +705,7 @@ walk_kernel(const WalkParams p)
                             atomicAdd(p.sims[sim].tally + MCX_TALLY_RR_GAINED, double((C.rr_m - R(1)) * w));
                         else
                             atomicAdd(&s_tally[MCX_TALLY_RR_GAINED], double((C.rr_m - R(1)) * w));
+                        gained += (C.rr_m - R(1)) * w;
                         w *= C.rr_m;
                         ++nrr;
                     } else {
@@ -720,6 +722,7 @@ walk_kernel(const WalkParams p)
 
         // ---- photon finished: flush the deposit run, tallies, logs, detectors (a9, a12)
         flush();
+        const R absorbed = R(1) + gained - w;
         const int slot = fate == MCX_FATE_ESCAPED ? MCX_TALLY_ESCAPED
                        : (fate == MCX_FATE_ROULETTE ? MCX_TALLY_RR_KILLED : MCX_TALLY_TIME);
         if constexpr (BATCH) {
