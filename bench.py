@@ -136,6 +136,17 @@ def peaks() -> dict:
     return p
 
 
+def walk_code_hash(path: str) -> str:
+    """sha256[:16] of a source file's code: '//' comments, trailing blanks and empty lines
+    removed, so that a change of comments alone keeps a capture valid."""
+    lines = []
+    for ln in open(path).read().splitlines():
+        ln = re.sub(r"//.*", "", ln).rstrip()
+        if ln.strip():
+            lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def walk_traffic(profile: str = "walk_kernel_c2.md", photons: int = None):
     """DRAM bytes per walk launch from the committed ncu summary, if it was taken on the
     current kernel source (matching hash); otherwise None.  A summary taken on fewer
@@ -145,9 +156,9 @@ def walk_traffic(profile: str = "walk_kernel_c2.md", photons: int = None):
     prof = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(prof):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = walk_code_hash(src)
     text = open(prof).read()
-    m_h = re.search(r"walk\.cu sha256\[:16\][^:\n]*:\s*([0-9a-f]{16})", text)
+    m_h = re.search(r"walk\.cu code sha256\[:16\][^:\n]*:\s*([0-9a-f]{16})", text)
     if not (m_h and m_h.group(1) == h):
         return None
     m_b = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)

@@ -19,8 +19,12 @@
 //    computed against 0 and 1, which keeps FP32 geometry at full precision anywhere in
 //    a large grid.
 //  * Absorbed weight is accumulated in a register while the photon stays in one
-//    (gate, voxel) and flushed with one fire-and-forget global atomic (RED.ADD.F32) when
-//    it leaves, instead of one atomic per segment.
+//    (gate, voxel) and flushed with one fire-and-forget global atomic when it leaves,
+//    instead of one atomic per segment: FP64 by default (the FP32 run total widened
+//    exactly in integer arithmetic), FP32 or compensated (hi, lo) pairs on request.
+//  * The current medium's constants (scattering, absorption, time per length, g) sit in
+//    registers and are reloaded only when the photon enters another label; a photon's
+//    absorbed weight is formed once, from its final weight and roulette gains.
 //  * Fast hardware math (MUFU ex2/lg2/sin/cos/rsqrt/rcp) in the FP32 path, the CUDA
 //    analogue of the paper's "native" math optimisation; the same kernel instantiated in
 //    FP64 serves as the trajectory-parity diagnostic.
@@ -279,8 +283,8 @@ template <> __device__ __forceinline__ const RunConsts<double> &consts<double>(c
 // without per-axis bounds checks, and the per-axis voxel indices need not be carried
 // (they are recovered from the linear index when a photon ends).  Caller-owned unpadded
 // buffers (the allocation-free run) take PAD = false.
-// FP32: 4 resident blocks of 256 threads per SM (64 registers; the batch instantiation fits
-// them too since the bordered volume freed its per-axis indices)
+// FP32: 4 resident blocks of 256 threads per SM (64 registers; the batch instantiation too,
+// with a few spilled words for its per-lane simulation geometry)
 template <typename R, bool DET, int ACC, bool STATIC, bool BATCH, bool PAD>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 1)
 walk_kernel(const WalkParams p)
