@@ -527,10 +527,12 @@ def study_denoise_kernels(args):
     t = x + 0.1 * torch.randn((nb,) + shape, device="cuda", generator=g)
     y = torch.empty_like(x)
     npos = [64 ** 3, 64 ** 3, 32 ** 3, 32 ** 3, 16 ** 3, 16 ** 3, 32 ** 3, 32 ** 3, 64 ** 3, 64 ** 3]
-    chans = [(16, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
+    # the input layer's one channel (no medium features) is its algorithmic work, not the
+    # 16 channels its padded weight gradient is computed on
+    chans = [(1, 16), (16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (96, 32), (32, 32), (48, 16), (16, 16)]
     fwd = sum(2 * p * 27 * ci * co for p, (ci, co) in zip(npos, chans))
     # a training step: forward, input gradients of every layer but the first, weight gradients
-    dgrad = fwd - 2 * npos[0] * 27 * 16 * 16
+    dgrad = fwd - 2 * npos[0] * 27 * 1 * 16
     with mcx.Denoiser(shape, max_batch=nb, seed=1) as d:
         def timed(fn):
             for _ in range(args.warmup):

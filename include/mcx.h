@@ -471,14 +471,16 @@ mcx_status mcx_debug_primitive(int32_t kind, uint64_t n, const float *in_host,
 mcx_status mcx_debug_wait_timeout(int32_t arrive, int32_t limit_log2, int32_t *timed_out);
 
 /* One 3x3x3 convolution of the denoiser on host arrays, run by the denoiser's own
-   tensor-core kernels (tcgen05 for kind 0, warp-level mma for kind 1); values are rounded
-   to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16 up to 254:
+   kernels (tcgen05 for kind 0 and kind 1; the direct input layer for kind 0 with cin 1);
+   values are rounded to BF16 on the way in; n volumes of nz x ny x nx, nx a multiple of 16
+   up to 254:
      kind 0: forward,  x [n][nz][ny][nx][cin], w [27][cout][cin], bias [cout] or NULL
              -> out = ReLU(conv + bias) [n][nz][ny][nx][cout], rounded to BF16
      kind 1: weight gradient, x as above, dy [n][nz][ny][nx][cout]
              -> out [27][cout][cin] = sum over positions of dy * x(shifted by the tap), FP32
    (cin, cout) one of the network's pairs: (16,16) (16,32) (16,48) (32,16) (32,32) (32,64)
-   (32,96) (48,16) (64,32) (64,64) (96,32). */
+   (32,96) (48,16) (64,32) (64,64) (96,32); for kind 0 also (1,16), the network's input
+   layer without medium features. */
 mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t nz, int32_t ny, int32_t nx,
                             int32_t cin, int32_t cout, const float *x, const float *w,
                             const float *bias, const float *dy, float *out);

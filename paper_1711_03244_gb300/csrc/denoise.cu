@@ -1039,6 +1039,77 @@ __global__ void pad_input(const float *x, const float *aux, int n_aux, int vol, 
     }
 }
 
+// input layer without medium features (one input channel): Y[p][co] = ReLU(b[co] +
+// sum_tap W[tap][co][0] x[p + off(tap)]), zero outside the volume.  The 16-channel
+// tensor-core path would multiply 15 zero input channels; here each thread forms the 16
+// outputs of 4 consecutive positions of a line (the width is a multiple of 16) from the
+// FP32 input, rounded to BF16 as the padded path stores it, with FP32 sums on the CUDA
+// cores: each input line segment is loaded once per (dz, dy) and each 4-channel weight
+// vector (shared memory) serves 16 products
+constexpr int kInThreads = 256;
+__global__ void __launch_bounds__(kInThreads, 2)
+conv_in_fwd(const float *__restrict__ x, const bf16 *__restrict__ W, const float *__restrict__ bias, Vol v,
+            bf16 *__restrict__ Y)
+{
+    __shared__ float4 sw[27][4];                  // W[tap][co][ci = 0], 4 channels per float4
+    __shared__ float sb[16];
+    for (int i = threadIdx.x; i < 27 * 16; i += blockDim.x)
+        reinterpret_cast<float *>(sw)[i] = __bfloat162float(W[(size_t)i * 16]);   // [27][16][16]
+    if (threadIdx.x < 16) sb[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+    __syncthreads();
+    const int nquad = (int)(v.pos() / 4), wq = v.w / 4;
+    auto rnd = [](float f) { return __bfloat162float(__float2bfloat16(f)); };
+    GRID_LOOP(qd, nquad) {
+        const int x0 = 4 * (qd % wq), r1 = qd / wq, yy = r1 % v.h, r2 = r1 / v.h, zz = r2 % v.d, b = r2 / v.d;
+        float acc[4][16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int co = 0; co < 16; ++co) acc[i][co] = sb[co];
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z2 = zz + dz;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y2 = yy + dy;
+                // the line's inputs at x0 - 1 .. x0 + 4 (zero outside the volume)
+                float xs[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if ((unsigned)z2 < (unsigned)v.d && (unsigned)y2 < (unsigned)v.h) {
+                    const float *line = x + ((size_t)(b * v.d + z2) * v.h + y2) * v.w;
+                    const float4 m = __ldg(reinterpret_cast<const float4 *>(line + x0));   // 16-B aligned
+                    xs[1] = rnd(m.x); xs[2] = rnd(m.y); xs[3] = rnd(m.z); xs[4] = rnd(m.w);
+                    if (x0 > 0) xs[0] = rnd(__ldg(line + x0 - 1));
+                    if (x0 + 4 < v.w) xs[5] = rnd(__ldg(line + x0 + 4));
+                }
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const int t = 9 * (dz + 1) + 3 * (dy + 1) + dx;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 wv = sw[t][q];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float xv = xs[i + dx];
+                            acc[i][4 * q] = fmaf(xv, wv.x, acc[i][4 * q]);
+                            acc[i][4 * q + 1] = fmaf(xv, wv.y, acc[i][4 * q + 1]);
+                            acc[i][4 * q + 2] = fmaf(xv, wv.z, acc[i][4 * q + 2]);
+                            acc[i][4 * q + 3] = fmaf(xv, wv.w, acc[i][4 * q + 3]);
+                        }
+                    }
+                }
+            }
+        }
+        bf16 *yo = Y + 16 * ((size_t)qd * 4);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int co = 0; co < 16; ++co) acc[i][co] = fmaxf(acc[i][co], 0.f);
+            st16(yo + 16 * i, Bf8::from(acc[i]).u);
+            st16(yo + 16 * i + 8, Bf8::from(acc[i] + 8).u);
+        }
+    }
+}
+
 // medium features of a label volume: log10(max(mua, 1e-4)) + 2 and
 // log10(max(mus (1 - g), 1e-3)), per voxel from a per-label table
 __global__ void features_kernel(const uint8_t *labels, int nvox, const float2 *tab, int n_media, float *out)
@@ -1284,6 +1355,10 @@ unsigned grid1(long long n)
 {
     return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 32));
 }
+
+// persistent grid of the direct input layer: the two resident blocks per SM that its
+// registers allow, so that each block's weight staging is paid once
+inline unsigned grid_in(long long positions) { return std::min(grid1(positions / 4), 152u * 2u); }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -1537,13 +1612,22 @@ static mcx_status forward(mcx_denoiser *d, const float *x, const float *aux, int
 {
     const Vol v0 = level_vol(d, 0, n), v1 = level_vol(d, 1, n), v2 = level_vol(d, 2, n);
     const float *P = d->params.as<float>();
-    pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, aux, d->n_aux, d->D * d->H * d->W, (int)v0.pos(),
-                                              d->x16.as<bf16>());
     auto conv = [&](int l, const bf16 *in, Vol v) {
         return launch_fwd_tc(in, kLayers[l].cin, d->wf[l].as<bf16>(), P + d->b_off[l], v,
                              kLayers[l].cout, 1, d->a[l].as<bf16>(), d->status.as<unsigned>(), st);
     };
-    DNC(d, conv(0, d->x16.as<bf16>(), v0), "conv e1a");
+    if (d->n_aux == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        // one input channel: the direct input layer, which reads the input in 16-byte
+        // vectors (the padded copy is made by the backward pass, which needs it for the
+        // layer's weight gradient)
+        conv_in_fwd<<<grid_in(v0.pos()), kInThreads, 0, st>>>(x, d->wf[0].as<bf16>(), P + d->b_off[0], v0,
+                                                          d->a[0].as<bf16>());
+        DNC(d, cudaGetLastError(), "conv e1a");
+    } else {
+        pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, aux, d->n_aux, d->D * d->H * d->W, (int)v0.pos(),
+                                                  d->x16.as<bf16>());
+        DNC(d, conv(0, d->x16.as<bf16>(), v0), "conv e1a");
+    }
     DNC(d, conv(1, d->a[0].as<bf16>(), v0), "conv e1b");
     avgpool_fwd<<<grid1(v1.pos() * 2), 256, 0, st>>>(d->a[1].as<bf16>(), v1, 16, d->p1.as<bf16>());
     DNC(d, conv(2, d->p1.as<bf16>(), v1), "conv e2a");
@@ -1615,6 +1699,9 @@ static mcx_status backward(mcx_denoiser *d, const float *x, const float *target,
     avgpool_bwd<<<grid1(v0.pos() * 2), 256, 0, st>>>(d->gp1.as<bf16>(), v0, 16, d->ga[1].as<bf16>());
     upcat_bwd_skip_add<<<grid1(v0.pos() * 2), 256, 0, st>>>(d->gu1.as<bf16>(), 32, 16, (int)v0.pos(), d->ga[1].as<bf16>());
     if ((s = conv_bwd(d, 1, d->a[0].as<bf16>(), v0, d->ga[0].as<bf16>(), st)) != MCX_OK) return s;
+    if (d->n_aux == 0)                  // the forward pass used the direct input layer
+        pad_input<<<grid1(v0.pos()), 256, 0, st>>>(x, nullptr, 0, d->D * d->H * d->W, (int)v0.pos(),
+                                                  d->x16.as<bf16>());
     if ((s = conv_bwd(d, 0, d->x16.as<bf16>(), v0, nullptr, st)) != MCX_OK) return s;
     DNC(d, cudaGetLastError(), "backward");
     return MCX_OK;
@@ -1892,6 +1979,31 @@ mcx_status mcx_debug_conv3d(int32_t kind, int32_t n, int32_t dd, int32_t hh, int
         return dn_fail(nullptr, MCX_E_ARG, "bad arguments");
     const Vol v{n, dd, hh, ww};
     const long long P = v.pos();
+    if (kind == 0 && cin == 1) {
+        // the direct input layer: FP32 input, weights [27][16][1] placed at ci = 0 of the
+        // network's [27][16][16] layout
+        if (cout != 16 || P * 96 >= (1LL << 31)) return dn_fail(nullptr, MCX_E_ARG, "bad arguments");
+        std::vector<bf16> hw16(27 * 16 * 16, __float2bfloat16(0.f));
+        for (int i = 0; i < 27 * 16; ++i) hw16[(size_t)i * 16] = __float2bfloat16(w[i]);
+        DBuf bx, bw, bb, by;
+        cudaError_t e = bx.alloc(P * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(bx.p, x, P * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = bw.alloc(hw16.size() * 2);
+        if (e == cudaSuccess) e = cudaMemcpy(bw.p, hw16.data(), hw16.size() * 2, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && bias) e = bb.alloc(16 * 4);
+        if (e == cudaSuccess && bias) e = cudaMemcpy(bb.p, bias, 16 * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = by.alloc(P * 16 * 2);
+        if (e == cudaSuccess) {
+            conv_in_fwd<<<grid_in(P), kInThreads>>>(bx.as<float>(), bw.as<bf16>(), bias ? bb.as<float>() : nullptr, v,
+                                                  by.as<bf16>());
+            e = cudaGetLastError();
+        }
+        std::vector<bf16> hy(P * 16);
+        if (e == cudaSuccess) e = cudaMemcpy(hy.data(), by.p, hy.size() * 2, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) for (size_t i = 0; i < hy.size(); ++i) out[i] = __bfloat162float(hy[i]);
+        if (e != cudaSuccess) return dn_fail(nullptr, MCX_E_CUDA, std::string("debug conv: ") + cudaGetErrorString(e));
+        return MCX_OK;
+    }
     std::vector<bf16> hx(P * cin), hw, hdy;
     for (long long i = 0; i < P * cin; ++i) hx[i] = __float2bfloat16(x[i]);
     DBuf bx, bw, bb, bdy, by, bdw;

@@ -78,6 +78,26 @@ def test_conv_forward_matches_oracle(g, cin, cout):
     assert np.array_equal(got, bf16(got))                 # outputs are BF16 values
 
 
+@pytest.mark.parametrize("shape", [(2, 3, 5, 48), (1, 9, 13, 32)])
+def test_input_layer_matches_oracle(g, shape):
+    """the direct input layer (one input channel, no medium features): FP32 sums of the 27
+    taps of the BF16-rounded input, so the same bound as the tensor-core convolutions"""
+    import torch
+    rng = np.random.default_rng(500 + shape[-1])
+    x = bf16(rng.normal(size=shape + (1,)))
+    w = bf16(rng.normal(size=(27, 16, 1)) / np.sqrt(27))
+    b = rng.normal(size=16).astype(np.float32)
+    got = g.mcx_debug_conv3d(0, x, w, b).astype(np.float64)
+    xt, wt = torch.tensor(x), torch.tensor(w)
+    ref = np.maximum(od.conv3d(xt, wt, torch.tensor(b, dtype=torch.float64)).numpy(), 0)
+    s_abs = od.conv3d(xt.abs(), wt.abs()).numpy() + np.abs(b)
+    bound = 2.0 ** -8 * np.abs(ref) + 1.01 * 27 * 2.0 ** -22 * s_abs
+    err = np.abs(got - ref)
+    print(f"input layer on {shape}: max err/bound {np.max(err / bound):.2f}")
+    assert np.all(err <= bound)
+    assert np.array_equal(got, bf16(got))
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 16), (48, 16)])
 def test_conv_forward_large_ragged_columns(g, cin, cout):
     """a volume large enough for multi-plane work units, with a depth (36) that leaves a
@@ -173,6 +193,30 @@ def test_network_forward_matches_oracle(g, torch_cuda, n_aux):
           f"{rel_exact:.2e}), max abs {np.abs(res_g - res_o).max():.2e} of {np.abs(res_o).max():.2e}")
     assert rel < 1e-2
     assert np.abs(res_g - res_o).max() < 5e-2 * np.abs(res_o).max()
+
+
+def test_network_forward_unaligned_input_takes_the_padded_path(g, torch_cuda):
+    """an input that does not start on a 16-byte boundary (a view one float into its
+    storage) runs the padded input layer instead of the direct one, which reads 16-byte
+    vectors; both match the oracle"""
+    torch = torch_cuda
+    rng = np.random.default_rng(13)
+    shape, n = (8, 8, 64), 2
+    p = random_params(rng)
+    x = rng.normal(size=(n,) + shape).astype(np.float32)
+    ref = od.forward(p.astype(np.float64), x.astype(np.float64), bf16=True).numpy()
+    with _net(g, shape, n, p) as d:
+        store = torch.empty(x.size + 1, device="cuda")
+        xd = store[1:].view((n,) + shape)
+        xd.copy_(torch.tensor(x, device="cuda"))
+        assert xd.data_ptr() % 16 != 0
+        yd = torch.empty_like(xd)
+        d.forward(xd, yd)
+        d.sync()
+        y = yd.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm((y - x) - (ref - x)) / np.linalg.norm(ref - x)
+    print(f"network forward, unaligned input: residual rel L2 {rel:.2e}")
+    assert rel < 1e-2
 
 
 def test_network_gradients_match_oracle(g, torch_cuda):
