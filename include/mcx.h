@@ -87,14 +87,13 @@ typedef struct mcx_run_cfg {
     int32_t accum_mode;            /* fluence accumulation; every mode first sums a photon's
                                       deposits in a register while it stays in one (gate, voxel):
                                       0: one FP32 atomic add per run into the map (fastest);
-                                      1: compensated FP32 pairs: runs inside the block tile (below)
-                                         go to a block-private shared-memory (hi, lo) pair, the
-                                         rounding error of each hi addition recovered exactly
-                                         (TwoSum on the atomic's old value) into lo; each block
-                                         flushes its tile once, in FP64, into the tile's FP64 map;
-                                         runs outside the tile go to a global (hi, lo) pair (the
-                                         two words adjacent) the same way; the result is
-                                         hi + lo + tile;
+                                      1: compensated FP32 pairs in block tiles: runs inside the
+                                         block tile (below) go to a block-private shared-memory
+                                         (hi, lo) pair, the rounding error of each hi addition
+                                         recovered exactly (TwoSum on the atomic's old value)
+                                         into lo; each block flushes its tile once, in FP64,
+                                         into the FP64 map; runs outside the tile go to that map
+                                         as in mode 2;
                                       2: FP64 global atomics (the default: exact to FP64
                                          rounding, and measured as fast as mode 0 on GB300,
                                          whose L2 adds FP64 at the FP32 rate; at 1e8 photons
@@ -199,8 +198,8 @@ mcx_status mcx_last_kernel_ms(mcx_sim *sim, float *ms);
 mcx_status mcx_read_fluence(mcx_sim *sim, float *dst, uint64_t n_elems, int32_t normalized,
                             int32_t dst_on_device);
 
-/* As mcx_read_fluence, in FP64: the map as accumulated (accum_mode 1: hi + lo + tile
-   summed in FP64; accum_mode 2: the FP64 map; accum_mode 0: the FP32 map widened). */
+/* As mcx_read_fluence, in FP64: the map as accumulated (accum_mode 1 and 2: the FP64 map,
+   with accum_mode 1's block tiles added into it; accum_mode 0: the FP32 map widened). */
 mcx_status mcx_read_fluence64(mcx_sim *sim, double *dst, uint64_t n_elems, int32_t normalized,
                               int32_t dst_on_device);
 

@@ -106,18 +106,14 @@ __global__ void finalize_kernel(const double *bt, const unsigned long long *bs, 
 
 // The fluence map as accumulated, in the caller's type, optionally normalised to fluence
 // rate per launched photon (x inv_norm[label], inv_norm = 1 / (mua h^3 N dt)):
-//   accum 0: the FP32 map;  accum 2: the FP64 map;
-//   accum 1: hi + lo of the interleaved pairs (+ the tile's FP64 sum inside the block
-//   tile), summed in FP64.
-struct TileBox {
-    int lo[4], size[4];
-};
+//   accum 0: the FP32 map;  accum 1 and 2: the FP64 map (accum 1 adds its block tiles
+//   into it when the walk ends).
 
 // The maps and labels carry the walk's one-voxel border ([g][nz+2][ny+2][nx+2]); the
 // output is unpadded [g][nz][ny][nx].
 template <typename T>
 __global__ void resolve_kernel(int mode, const float *hi, const double *f64,
-                               TileBox tb, unsigned nx, unsigned ny, unsigned nvox, unsigned pnvox,
+                               unsigned nx, unsigned ny, unsigned nvox, unsigned pnvox,
                                unsigned n_gates, const uint8_t *labels, const float *inv_norm,
                                T *out)
 {
@@ -135,17 +131,7 @@ __global__ void resolve_kernel(int mode, const float *hi, const double *f64,
             out[i] = (T)f;
             continue;
         }
-        double d;
-        if (mode == 2) {
-            d = f64[pi];
-        } else {
-            d = (double)hi[2 * pi] + (double)hi[2 * pi + 1];     // interleaved (hi, lo)
-            const unsigned tx = x - (unsigned)tb.lo[0], ty = y - (unsigned)tb.lo[1];
-            const unsigned tz = z - (unsigned)tb.lo[2], tg = g - (unsigned)tb.lo[3];
-            if (tx < (unsigned)tb.size[0] && ty < (unsigned)tb.size[1] &&
-                tz < (unsigned)tb.size[2] && tg < (unsigned)tb.size[3])
-                d += f64[((tg * tb.size[2] + tz) * tb.size[1] + ty) * tb.size[0] + tx];
-        }
+        double d = f64[pi];
         if (inv_norm) d *= (double)inv_norm[labels[pv]];
         out[i] = (T)d;
     }
@@ -238,7 +224,6 @@ struct mcx_sim {
 
     DevBuf labels, fluence, fluence64, tables, detb, det_buf, exits, block_tally,
         block_stats, ctrl, out, staging, inv_norm, sort_keys, sort_vals;
-    int tile_lo[4] = {0, 0, 0, 0}, tile_size[4] = {0, 0, 0, 0};
     std::vector<unsigned char> host_tables;
 
     // last run
@@ -540,14 +525,11 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     const uint64_t nvox = (uint64_t)(s->nx + 2) * (s->ny + 2) * (s->nz + 2);
     const uint64_t nflu = nvox * cfg->n_gates;
     const int stride = kRecBase + (int)s->n_media - 1;
-    // accum 1 keeps each voxel's (hi, lo) pair in adjacent words
-    const uint64_t nflu32 = accum == kAccCompensated ? 2 * nflu : nflu;
+    // accum 0 accumulates into the FP32 map, accum 1 and 2 into the FP64 one
+    const uint64_t nflu32 = accum == kAccPlain ? nflu : 1;
     MCX_CUDA(s, s->fluence.ensure(nflu32 * sizeof(float)), "allocating the fluence map");
-    if (accum == kAccCompensated) {
-        MCX_CUDA(s, s->fluence64.ensure((size_t)std::max(tile_e, 1) * sizeof(double)), "allocating the tile map");
-    } else if (accum == kAccF64) {
+    if (accum != kAccPlain)
         MCX_CUDA(s, s->fluence64.ensure(nflu * sizeof(double)), "allocating the FP64 fluence map");
-    }
     MCX_CUDA(s, s->block_tally.ensure((size_t)shape.grid * MCX_NTALLY * sizeof(double)), "allocating");
     MCX_CUDA(s, s->block_stats.ensure((size_t)shape.grid * MCX_NSTAT * 8), "allocating");
     MCX_CUDA(s, s->ctrl.ensure(64), "allocating");
@@ -646,13 +628,10 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     p.claim_chunk = kClaimChunk;
 
     // zero the outputs, walk, reduce
-    zero_words<<<grid_for(nflu32 / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu32);
-    if (accum == kAccCompensated) {
-        zero_words<<<grid_for((size_t)tile_e / 2 + 1), 256, 0, st>>>(s->fluence64.as<uint32_t>(),
-                                                                     (size_t)std::max(tile_e, 1) * 2);
-    } else if (accum == kAccF64) {
+    if (accum == kAccPlain)
+        zero_words<<<grid_for(nflu32 / 4 + 1), 256, 0, st>>>(s->fluence.as<uint32_t>(), (size_t)nflu32);
+    else
         zero_words<<<grid_for(nflu / 2 + 1), 256, 0, st>>>(s->fluence64.as<uint32_t>(), (size_t)nflu * 2);
-    }
     zero_words<<<1, 32, 0, st>>>(s->ctrl.as<uint32_t>(), 16);
     if (cfg->exit_log > 0)
         zero_words<<<grid_for(cfg->exit_log * 10 / 4 + 1), 256, 0, st>>>(
@@ -669,10 +648,6 @@ mcx_status mcx_run(mcx_sim *s, const mcx_run_cfg *cfg)
     MCX_CUDA(s, cudaEventRecord(s->ev_done, st), "recording an event");
 
     s->cfg = *cfg;
-    for (int a = 0; a < 4; ++a) {
-        s->tile_lo[a] = tlo[a];
-        s->tile_size[a] = tsz[a];
-    }
     s->shape = shape;
     s->rec_stride = stride;
     s->stream = st;
@@ -761,13 +736,8 @@ static mcx_status read_fluence_t(mcx_sim *s, T *dst, uint64_t n_elems, int32_t n
         MCX_CUDA(s, s->staging.ensure(n * sizeof(T)), "allocating the staging buffer");
         out = static_cast<T *>(s->staging.p);
     }
-    TileBox tb;
-    for (int a = 0; a < 4; ++a) {
-        tb.lo[a] = s->tile_lo[a];
-        tb.size[a] = s->tile_size[a];
-    }
     resolve_kernel<T><<<grid_for(n), 256, 0, st>>>(mode, s->fluence.as<float>(),
-                                                   s->fluence64.as<double>(), tb, s->nx, s->ny,
+                                                   s->fluence64.as<double>(), s->nx, s->ny,
                                                    (unsigned)nvox, (unsigned)pnvox, s->cfg.n_gates,
                                                    s->labels.as<uint8_t>(), inv_dev, out);
     MCX_CUDA(s, cudaGetLastError(), "launching the fluence read-out");

@@ -389,21 +389,26 @@ walk_kernel(const WalkParams p)
     auto flush = [&]() {
         if (acc != R(0)) {
             const unsigned long long idx = (unsigned long long)gate * G_nvox + vlin;
-            if (ACC == kAccPlain) {
-                atomicAdd(G_flu + idx, float(acc));
-            } else if (ACC == kAccF64) {
+            // one fire-and-forget FP64 add into the map; for FP32 the (positive, normal: the
+            // walk flushes denormals) run total is widened exactly in integer arithmetic:
+            // exponent rebiased by 1023 - 127 = 896, mantissa shifted by 29 (measured 0.9%
+            // faster than the conversion instruction, which runs on the narrow FP64 pipe)
+            auto add_f64 = [&]() {
                 if (sizeof(R) == 4) {
-                    // exact FP32 -> FP64 widening of the (positive, normal: the walk flushes
-                    // denormals) run total in integer arithmetic: exponent rebiased by
-                    // 1023 - 127 = 896, mantissa shifted by 29 (measured 0.9% faster than the
-                    // conversion instruction, which runs on the narrow FP64 pipe)
                     const unsigned f = __float_as_uint(float(acc));
                     const double dv = __hiloint2double((int)((f >> 3) + (896u << 20)), (int)(f << 29));
                     atomicAdd(G_flu64 + idx, dv);
                 } else {
                     atomicAdd(G_flu64 + idx, double(acc));
                 }
+            };
+            if (ACC == kAccPlain) {
+                atomicAdd(G_flu + idx, float(acc));
+            } else if (ACC == kAccF64) {
+                add_f64();
             } else {
+                // compensated: runs inside the block tile go to its shared-memory (hi, lo)
+                // pair, the rest to the FP64 map
                 const unsigned tx = (unsigned)(ix - p.tile_lo[0]), ty = (unsigned)(iy - p.tile_lo[1]);
                 const unsigned tz = (unsigned)(iz - p.tile_lo[2]), tg = gate - (unsigned)p.tile_lo[3];
                 if (tx < (unsigned)p.tile_size[0] && ty < (unsigned)p.tile_size[1] &&
@@ -412,8 +417,7 @@ walk_kernel(const WalkParams p)
                                        p.tile_size[0] + tx;
                     pair_add(s_hi + k, s_lo + k, float(acc));
                 } else {
-                    // the map's (hi, lo) words are adjacent: both additions touch one sector
-                    pair_add(p.fluence + 2 * idx, p.fluence + 2 * idx + 1, float(acc));
+                    add_f64();
                 }
             }
             ++c_flush;
@@ -797,10 +801,16 @@ walk_kernel(const WalkParams p)
 
     __syncthreads();
     if (ACC == kAccCompensated) {
-        // the block's tile, flushed once in FP64 into the tile's map
+        // the block's tile, flushed once in FP64 into the map at its (gate, voxel) positions
+        const int s0 = p.tile_size[0], s1 = p.tile_size[1], s2 = p.tile_size[2];
+        constexpr unsigned B = PAD ? 1u : 0u;          // the map's border
         for (int k = threadIdx.x; k < tile_e; k += blockDim.x) {
             const double v = (double)s_hi[k] + (double)s_lo[k];
-            if (v != 0.0) atomicAdd(p.fluence64 + k, v);
+            if (v == 0.0) continue;
+            const int tx = k % s0, ty = (k / s0) % s1, tz = (k / (s0 * s1)) % s2, tg = k / (s0 * s1 * s2);
+            const unsigned vl = (unsigned)(p.tile_lo[2] + tz + B) * G_sz + (unsigned)(p.tile_lo[1] + ty + B) * G_sy +
+                                (unsigned)(p.tile_lo[0] + tx + B);
+            atomicAdd(G_flu64 + (unsigned long long)(p.tile_lo[3] + tg) * G_nvox + vl, v);
         }
     }
     if (threadIdx.x < MCX_NTALLY)
