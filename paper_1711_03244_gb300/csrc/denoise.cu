@@ -128,7 +128,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int kTcRows = 128, kTcThreads = 192, kTcHeader = 256, kTcFwdHeader = 384;
+constexpr int kTcRows = 128, kTcThreads = 192, kTcFwdHeader = 384;
 constexpr int kTcWallMax = 64 * 1024;       // weights up to this size stay resident
 constexpr int kTcSmemBudget = 112 * 1024;   // preferred shared memory per CTA
 constexpr int kTcSmemMax = 227 * 1024;      // shared memory one CTA may use
@@ -404,33 +404,33 @@ conv3d_fwd_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
                     if (j >= 2) tc_commit(accf0 + 8 * ((T0 + j - 2) & (NSLOT - 1)));   // tile j - 2 is complete
                     tc_commit(empty0 + 8 * b);
                     if (++b == ns) { b = 0; ++use; }
-                    continue;
-                }
-                // tiles i of the unit reading this plane, the finishing one first: dz = j - 1 - i
-                for (int i = j - 2; i <= j; ++i) {
-                    if (i < 0 || i >= U.nz) continue;
-                    const int dz = j - 1 - i, T = T0 + i, slot = T & (NSLOT - 1);
-                    if (dz == -1 && T >= NSLOT)                 // the slot's previous tile is read out
-                        ok &= mbar_wait(acce0 + 8 * slot, (uint32_t)((T / NSLOT - 1) & 1));
-                    if (!ok) break;
-                    const uint64_t bbase = WALL ? bdesc0 + (uint64_t)((9 * (dz + 1) * wtap) >> 4)
-                                                : bdesc0 + (uint64_t)((b * stage_bytes) >> 4);
-                    const uint32_t d = tmem + slot * NCOL;
+                } else {
+                    // tiles i of the unit reading this plane, the finishing one first: dz = j - 1 - i
+                    for (int i = j - 2; i <= j; ++i) {
+                        if (i < 0 || i >= U.nz) continue;
+                        const int dz = j - 1 - i, T = T0 + i, slot = T & (NSLOT - 1);
+                        if (dz == -1 && T >= NSLOT)                 // the slot's previous tile is read out
+                            ok &= mbar_wait(acce0 + 8 * slot, (uint32_t)((T / NSLOT - 1) & 1));
+                        if (!ok) break;
+                        const uint64_t bbase = WALL ? bdesc0 + (uint64_t)((9 * (dz + 1) * wtap) >> 4)
+                                                    : bdesc0 + (uint64_t)((b * stage_bytes) >> 4);
+                        const uint32_t d = tmem + slot * NCOL;
 #pragma unroll
-                    for (int tt = 0; tt < 9; ++tt)              // tt = 3 (dy + 1) + (dx + 1)
+                        for (int tt = 0; tt < 9; ++tt)              // tt = 3 (dy + 1) + (dx + 1)
 #pragma unroll
-                        for (int kk = 0; kk < CIN / 16; ++kk) {
-                            const uint64_t ad = sw32_desc(abase + (uint32_t)(toff[tt] * 32 + kk * lbo_a));
-                            const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
-                            const uint32_t accum = (dz == -1 && tt == 0 && kk == 0) ? 0u : 1u;
-                            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                                         ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
-                        }
-                    if (dz == 1) tc_commit(accf0 + 8 * slot);    // tile i is complete
+                            for (int kk = 0; kk < CIN / 16; ++kk) {
+                                const uint64_t ad = sw32_desc(abase + (uint32_t)(toff[tt] * 32 + kk * lbo_a));
+                                const uint64_t bd = bbase + (uint64_t)((tt * wtap + 2 * kk * lbo_b) >> 4);
+                                const uint32_t accum = (dz == -1 && tt == 0 && kk == 0) ? 0u : 1u;
+                                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                             ::"r"(d), "l"(ad), "l"(bd), "r"(IDESC), "r"(accum) : "memory");
+                            }
+                        if (dz == 1) tc_commit(accf0 + 8 * slot);    // tile i is complete
+                    }
+                    tc_commit(empty0 + 8 * b);
+                    if (++b == ns) { b = 0; ++use; }
                 }
-                tc_commit(empty0 + 8 * b);
-                if (++b == ns) { b = 0; ++use; }
             }
             T0 += U.nz;
         }
