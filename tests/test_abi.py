@@ -101,6 +101,13 @@ def test_denoiser_and_batch_argument_errors(lib):
     assert L.mcx_denoiser_encode(None, None, None, 0, None) == m.MCX_E_ARG
     assert L.mcx_denoiser_decode(None, None, None, 0, None) == m.MCX_E_ARG
     assert L.mcx_denoiser_apply(None, None, None, None, 1, None) == m.MCX_E_ARG
+    # the debug convolution: the direct input layer takes cin 1 with cout 16 only, and every
+    # kind needs a width that is a multiple of 16 (checked before any device work)
+    f = (ctypes.c_float * 64)()
+    assert L.mcx_debug_conv3d(0, 1, 1, 1, 16, 1, 32, f, f, None, None, f) == m.MCX_E_ARG
+    assert L.mcx_debug_conv3d(0, 1, 1, 1, 12, 1, 16, f, f, None, None, f) == m.MCX_E_ARG
+    assert L.mcx_debug_conv3d(2, 1, 1, 1, 16, 16, 16, f, f, None, None, f) == m.MCX_E_ARG
+    assert L.mcx_debug_conv3d(1, 1, 1, 1, 16, 16, 16, f, None, None, None, f) == m.MCX_E_ARG
     assert L.mcx_denoiser_sync(None) == m.MCX_E_ARG
     L.mcx_denoiser_destroy(None)
     assert L.mcx_batch_create(None) == m.MCX_E_ARG
